@@ -1,0 +1,436 @@
+"""Benchmark of the nested-grid lattice Boltzmann hot path on GB300.
+
+Headline workload: 256^3 periodic decaying turbulence (random-phase
+solenoidal field, E(k) ~ k^4 exp(-2 (k/k0)^2), k0 = 4, u_rms = 0.04,
+nu = 1e-4), D3Q27 factorized cascaded collision, FP32 storage.  One "step" is
+one coarse time step (one fused stream-collide launch over all 16.8 M cells
+in a CUDA graph).  Metric: MLUPS (million lattice-cell updates per second),
+with the HBM-roofline fraction of the stream-collide kernel at 216 algorithmic
+bytes per FP32 D3Q27 update (27 values read + 27 written).
+
+Also reported ("variants"): FP16 storage and D3Q19 MRT-LES on the same grid,
+the 2-level round-jet grid (coarse 384x192x192, fine cylinder of radius 24
+coarse cells), the FP64-storage run, and the velocity error of FP32 / FP16
+storage against the FP64 run after a fixed number of steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per GPU, launched by torchrun): the
+update has no exchange step on one GPU, so there is no collective; value is
+the whole-job MLUPS (all replicas' updates / the max time over ranks).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline, FP32/FP16-storage vs FP64 at stated error"
+N_GRID = 256
+NU = 1e-4
+OMEGA = 1.0 / (3.0 * NU + 0.5)
+BYTES_PER_UPDATE = {("d3q27", "f32"): 216, ("d3q27", "f16"): 108, ("d3q27", "f64"): 432,
+                    ("d3q19", "f32"): 152, ("d3q19", "f16"): 76, ("d3q19", "f64"): 304}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "update_kernel_traffic.txt")
+KERNEL_SOURCES = ["paper_1206_0389_gb300/csrc/update.cu", "paper_1206_0389_gb300/csrc/collide.cuh",
+                  "paper_1206_0389_gb300/csrc/lattice.cuh", "paper_1206_0389_gb300/csrc/kernels.cuh"]
+
+
+# ----------------------------------------------------------------- distributed helpers
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value, device=None):
+    """Max of a float over ranks (identity on one rank)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value, device=None):
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def whole_job_mlups(updates_all_ranks, max_ms):
+    return updates_all_ranks / (max_ms * 1e-3) / 1e6
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- roofline inputs
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_update(model, storage):
+    """DRAM bytes per cell update from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    kv = {}
+    for line in open(TRAFFIC_FILE):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_sha") != kernel_sha():
+        return None
+    key = "bytes_per_update_%s_%s" % (model, storage)
+    return float(kv[key]) if key in kv else None
+
+
+# ----------------------------------------------------------------- our arm
+def run_uniform(lbm, torch, model, storage, field, steps, warmup, stream, sampler=None):
+    """Time `steps` coarse steps of the 256^3 periodic grid; returns a dict."""
+    nb = (N_GRID // 8,) * 3
+    ctx = lbm.lbm_create(model, storage, nb, True, [], OMEGA, 0.1 if model == "d3q19" else 0.0,
+                         stream.cuda_stream)
+    rho, u = field
+    lbm.lbm_init_equilibrium(ctx, 0, rho, u)
+    lbm.lbm_step(ctx, warmup)
+    lbm.lbm_sync(ctx)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if sampler:
+        sampler.start()
+    e0.record(stream)
+    lbm.lbm_step(ctx, steps)
+    e1.record(stream)
+    e1.synchronize()
+    clocks = sampler.stop() if sampler else None
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    # profiled pass: per-launch CUDA events around each kernel on the same stream
+    lbm.lbm_set_profiling(ctx, True)
+    prof_steps = max(5, min(steps, 50))
+    lbm.lbm_step(ctx, prof_steps)
+    pms, pn = lbm.lbm_get_profile(ctx)
+    lbm.lbm_set_profiling(ctx, False)
+    threads, ctas = lbm.lbm_get_tuning(ctx)
+    out = dict(ctx=ctx, ms=ms, clocks=clocks, kernel_ms=pms[0] / max(pn[0], 1),
+               launches_per_step=int(pn.sum()) // prof_steps, tuning=(threads, ctas),
+               cells=N_GRID ** 3)
+    return out
+
+
+def roofline(model, storage, kernel_ms, cells):
+    peak, src = measured_peak()
+    bpu = BYTES_PER_UPDATE[(model, storage)]
+    achieved = bpu * cells / (kernel_ms * 1e-3) / 1e9
+    t = ncu_traffic_per_update(model, storage)
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": src,
+            "traffic": None if t is None else round(t * cells),
+            "algorithmic_bytes_per_launch": bpu * cells}
+
+
+def velocity_error(lbm, ctx, ref_u):
+    _, u = lbm.lbm_macroscopic(ctx, 0)
+    return float(np.sqrt(((u - ref_u) ** 2).sum() / (ref_u ** 2).sum()))
+
+
+def run_jet(lbm, torch, model, steps, warmup, stream):
+    import synth
+    flags, centre = synth.jet_two_level()
+    nu_c = 0.05 * 16 / 1e4
+    ctx = lbm.lbm_create(model, "f32", (48, 24, 24), False, flags, 1.0 / (3 * nu_c + 0.5),
+                         0.18 if model == "d3q19" else 0.0, stream.cuda_stream)
+    lbm.lbm_set_inflow(ctx, centre[0], centre[1], 16.0, 0.05, 0.01, 389)
+    info = lbm.lbm_plan((48, 24, 24), False, flags, model, "f32")
+    lbm.lbm_step(ctx, warmup)
+    lbm.lbm_sync(ctx)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lbm.lbm_step(ctx, steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    lbm.lbm_set_profiling(ctx, True)
+    lbm.lbm_step(ctx, 3)
+    pms, pn = lbm.lbm_get_profile(ctx)
+    lbm.lbm_destroy(ctx)
+    upd = info.active_updates_per_coarse_step
+    peak, _ = measured_peak()
+    bpu = BYTES_PER_UPDATE[(model, "f32")]
+    return {"mlups": round(upd / (ms * 1e-3) / 1e6, 1), "ms_per_coarse_step": round(ms, 4),
+            "active_updates_per_coarse_step": int(upd),
+            "frac_of_hbm_roofline": round(bpu * upd / (ms * 1e-3) / 1e9 / peak, 4),
+            "profile_ms_per_coarse_step": {k: round(float(v) / 3, 4) for k, v in
+                                           zip(["update", "c2f", "f2c", "bc", "other"], pms)},
+            "launches_per_coarse_step": int(pn.sum()) // 3}
+
+
+def cpu_baseline(seconds=12.0):
+    """The FP64 oracle as it stands on the host cores: D3Q27 FCLB on a 16^3
+    periodic sample of the decaying-turbulence workload."""
+    import torch
+    import synth
+    from oracle.solver import NestedSolver
+    s = NestedSolver("d3q27", (2, 2, 2), periodic_x=True, omega=OMEGA)
+    rho, u = synth.spectrum_field(16, seed=1206)
+    s.init_equilibrium(0, torch.from_numpy(rho), torch.from_numpy(u))
+    s.step(1)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        s.step(1)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds and n >= 2:
+            break
+    return {"value": round(16 ** 3 * n / dt / 1e6, 6), "unit": "MLUPS", "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": "D3Q27 FCLB FP64 oracle, 16^3 periodic sample of the k^4-spectrum field, %d steps in %.1f s" % (n, dt)}
+
+
+def ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    import synth
+    import __graft_entry__
+    __graft_entry__.build() if not os.path.exists(
+        os.path.join(ROOT, "paper_1206_0389_gb300", "liblbm.so")) else None
+    from paper_1206_0389_gb300 import lbm
+    stream = torch.cuda.Stream()
+    field = synth.spectrum_field(N_GRID, seed=1206 + rank)
+    K, W = args.steps, args.warmup
+
+    # headline: D3Q27 FCLB FP32
+    barrier(dist)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    head = run_uniform(lbm, torch, "d3q27", "f32", field, K, W, stream, sampler)
+    barrier(dist)
+    ms_max = max_over_ranks(dist, head["ms"], device="cuda")
+    updates_all = sum_over_ranks(dist, head["cells"] * K, device="cuda")
+    value = whole_job_mlups(updates_all, ms_max)
+    roof = roofline("d3q27", "f32", head["kernel_ms"], head["cells"])
+    ctx = head["ctx"]
+    lbm.lbm_destroy(ctx)
+
+    # end to end through the C ABI with host buffers: upload the initial field
+    # from pinned memory, K steps each followed by the float64 audit read
+    # back to the host, then the macroscopic field back to pinned memory
+    rho_h = torch.from_numpy(field[0]).pin_memory()
+    u_h = torch.from_numpy(field[1]).pin_memory()
+    rho_o = torch.empty_like(rho_h).pin_memory()
+    u_o = torch.empty_like(u_h).pin_memory()
+    ctx = lbm.lbm_create("d3q27", "f32", (32, 32, 32), True, [], OMEGA, 0.0, stream.cuda_stream)
+    lbm.lbm_step(ctx, 1)
+    lbm.lbm_sync(ctx)
+    barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lib = lbm.load()
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    st = lib.lbm_init_equilibrium(ctx.h, 0, ctypes.cast(rho_h.data_ptr(), dp), ctypes.cast(u_h.data_ptr(), dp))
+    assert st == 0, lbm.lbm_last_error(ctx)
+    audit = np.empty(4)
+    for _ in range(K):
+        lbm.lbm_step(ctx, 1)
+        st = lib.lbm_mass_momentum(ctx.h, audit.ctypes.data_as(dp))
+        assert st == 0, lbm.lbm_last_error(ctx)
+    st = lib.lbm_macroscopic(ctx.h, 0, ctypes.cast(rho_o.data_ptr(), dp), ctypes.cast(u_o.data_ptr(), dp))
+    assert st == 0, lbm.lbm_last_error(ctx)
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    lbm.lbm_destroy(ctx)
+    barrier(dist)
+    e2e_max = max_over_ranks(dist, e2e_ms, device="cuda")
+    cells = N_GRID ** 3
+    h2d = 4 * cells * 8
+    d2h = 4 * cells * 8 + 32 * K
+    e2e = {"value": round(whole_job_mlups(updates_all, e2e_max), 1), "unit": "MLUPS",
+           "h2d_bytes_per_step": int(h2d / K), "d2h_bytes_per_step": int(d2h / K),
+           "what": "init from pinned host rho/u + K x (step + float64 audit to host) + rho/u to pinned host"}
+
+    variants = {}
+    errors = {}
+    if not args.quick:
+        # FP64 reference run and storage error after a fixed number of steps
+        E = 100
+        ref = run_uniform(lbm, torch, "d3q27", "f64", field, E, 0, stream)
+        _, ref_u = lbm.lbm_macroscopic(ref["ctx"], 0)
+        variants["d3q27_f64"] = {"mlups": round(cells * E / (ref["ms"] * 1e-3) / 1e6, 1),
+                                 "roofline_frac": roofline("d3q27", "f64", ref["kernel_ms"], cells)["frac"]}
+        lbm.lbm_destroy(ref["ctx"])
+        for model, storage in (("d3q27", "f16"), ("d3q19", "f32"), ("d3q19", "f16")):
+            r = run_uniform(lbm, torch, model, storage, field, K, W, stream)
+            rf = roofline(model, storage, r["kernel_ms"], cells)
+            variants["%s_%s" % (model, storage)] = {
+                "mlups": round(cells * K / (r["ms"] * 1e-3) / 1e6, 1), "roofline_frac": rf["frac"],
+                "achieved_gbs": rf["achieved"], "tuning": list(r["tuning"])}
+            lbm.lbm_destroy(r["ctx"])
+        for storage in ("f32", "f16"):
+            r = run_uniform(lbm, torch, "d3q27", storage, field, E, 0, stream)
+            errors["d3q27_%s_vs_f64_velocity_rel_l2_after_%d_steps" % (storage, E)] = \
+                velocity_error(lbm, r["ctx"], ref_u)
+            lbm.lbm_destroy(r["ctx"])
+        for model in ("d3q27", "d3q19"):
+            variants["jet_2level_%s_f32" % model] = run_jet(lbm, torch, model, max(10, K // 4), 3, stream)
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": round(ms_max / K, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "256^3 periodic decaying turbulence, D3Q27 FCLB, FP32 storage "
+                               "(k^4 spectrum, k0=4, u_rms=0.04, nu=1e-4)",
+                   "cells": cells, "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (1.81 GB per distribution buffer)",
+                   "launch": {"threads": head["tuning"][0], "ctas": head["tuning"][1]}},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": head["launches_per_step"] * K,
+        "clocks": head["clocks"],
+        "kernel_ms": round(head["kernel_ms"], 4),
+        "variants": variants,
+        "storage_error": errors,
+    }
+    if rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def reference(args):
+    """The oracle timed on the host cores on the same metric (bounded sample)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import torch
+    import synth
+    from oracle.solver import NestedSolver
+    s = NestedSolver("d3q27", (2, 2, 2), periodic_x=True, omega=OMEGA)
+    rho, u = synth.spectrum_field(16, seed=1206)
+    s.init_equilibrium(0, torch.from_numpy(rho), torch.from_numpy(u))
+    for _ in range(args.warmup):
+        s.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step(1)
+    dt = time.perf_counter() - t0
+    v = 16 ** 3 * args.steps / dt / 1e6
+    cb = {"value": round(v, 6), "unit": "MLUPS", "cores": torch.get_num_threads(), "kind": "oracle",
+          "sample": "D3Q27 FCLB FP64 oracle, 16^3 periodic sample of the 256^3 k^4-spectrum workload, "
+                    "%d steps" % args.steps}
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "MLUPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "256^3 periodic decaying turbulence, D3Q27 FCLB (16^3 sample on the host)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": round(v, 6), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--quick", action="store_true", help="headline only (no variants)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

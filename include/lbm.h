@@ -1,0 +1,179 @@
+/*
+ * lbm.h - C ABI of the GB300 nested-grid lattice Boltzmann library (liblbm.so).
+ *
+ * The library advances the fused stream-and-collide update of
+ *   - D3Q19 MRT with a Smagorinsky eddy viscosity (Section 2: Eqs. MRT,
+ *     relaxationTau, eqSmago, eqStrainRate, eqTauTotFinal, EqnQ; Table 1), and
+ *   - D3Q27 factorized cascaded (central-moment) collision (Section 2, Table 2),
+ * on a block-structured grid of 8^3-cell blocks with time-nested 2:1
+ * refinement after Yu et al. (Sections 1 and 3.2).  All arithmetic runs in
+ * CUDA kernels on the calling thread's current device.
+ *
+ * Conventions for every entry point
+ *   - Return value: LBM_OK (0) or a negative lbm_status.  Nothing throws.
+ *     lbm_last_error() returns a message for the last failure on a context.
+ *   - The context owns all device memory it allocates.  The caller owns every
+ *     buffer it passes; host buffers may be pageable or pinned.
+ *   - Calls are ordered on the context's stream.  lbm_step() only enqueues
+ *     work; every call that returns data to the host synchronises the stream.
+ *   - Dense per-level arrays are row-major with x fastest: index
+ *     x + NX_l * (y + NY_l * z), NX_l = 8 * nbx * 2^l (likewise y, z).
+ *     Distribution arrays are [Q][NZ_l][NY_l][NX_l] in the velocity order of
+ *     the paper's D3Q19 / D3Q27 tables, vectors [3][NZ_l][NY_l][NX_l].
+ *   - Distributions exchanged with the host are float64 and unshifted: the
+ *     D3Q19 model stores the incompressible distribution whose sum is
+ *     delta rho (Section 2), the D3Q27 model the full distribution (sum rho).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_MAX_LEVELS 4
+#define LBM_BLOCK 8
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,       /* invalid argument or grid; nothing was changed        */
+  LBM_ERR_OOM = -2,       /* device or host allocation failed                      */
+  LBM_ERR_CUDA = -3,      /* a CUDA call failed (no device, launch error, ...)     */
+  LBM_ERR_TIMEOUT = -4,   /* reserved: a bounded device wait gave up               */
+  LBM_ERR_NONFINITE = -5, /* NaN/Inf in an input or in the audited state          */
+  LBM_ERR_STATE = -6      /* call not valid in the context's current state        */
+} lbm_status;
+
+typedef enum { LBM_D3Q19_MRT_LES = 0, LBM_D3Q27_FCLB = 1 } lbm_model;
+
+/* Storage of the distributions in device memory.  They are stored shifted by
+ * the lattice weights (f_i - w_i for D3Q27; the D3Q19 incompressible
+ * distribution is already a fluctuation); F16 stores (f_i - w_i)/w_i.
+ * Collision arithmetic is float64 for F64 and float32 otherwise. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2 } lbm_storage;
+
+/* Block grid.  Level 0 has nbx*nby*nbz blocks of 8^3 cells; y and z are
+ * periodic.  x is periodic when periodic_x != 0; otherwise the face x = 0 is a
+ * velocity inflow (lbm_set_inflow; rest velocity until called) and the face
+ * x = NX a zero-gradient outflow.  refine concatenates, for l = 0..levels-2,
+ * one byte per level-l block (nbx*2^l by nby*2^l by nbz*2^l, x fastest):
+ * 1 = the block is split into 8 level-(l+1) blocks.  Rules (checked):
+ * flags only on blocks of level l; each level l < levels-1 refines at least
+ * one block; for l >= 1 every block touching a refined block belongs to
+ * level l (so interpolation stencils stay inside level l). */
+typedef struct {
+  int nbx, nby, nbz;
+  int periodic_x;
+  int levels;
+  const uint8_t* refine;
+} lbm_grid;
+
+/* Sizes of a grid, computed on the host without touching a GPU. */
+typedef struct {
+  int levels;
+  int64_t blocks[LBM_MAX_LEVELS];        /* allocated blocks (level + ghost blocks) */
+  int64_t level_blocks[LBM_MAX_LEVELS];  /* blocks belonging to the level           */
+  int64_t active_cells[LBM_MAX_LEVELS];  /* cells of unrefined level blocks         */
+  int64_t updated_cells[LBM_MAX_LEVELS]; /* active + hidden layer 1                 */
+  int64_t hidden_cells[LBM_MAX_LEVELS];  /* hidden layers 1 and 2                   */
+  int64_t ghost_cells[LBM_MAX_LEVELS];   /* coarse-to-fine ghost cells              */
+  int64_t bc_cells[LBM_MAX_LEVELS];      /* inflow/outflow ghost cells              */
+  int64_t updates_per_coarse_step;       /* sum_l updated_cells[l] * 2^l            */
+  int64_t active_updates_per_coarse_step;/* sum_l active_cells[l] * 2^l             */
+  int64_t device_bytes;                  /* device memory lbm_create would allocate */
+} lbm_plan_info;
+
+/* Plan a grid on the host (no CUDA call).  Validates g like lbm_create.
+ * model/storage are lbm_model/lbm_storage values (they set device_bytes). */
+int lbm_plan(const lbm_grid* g, int model, int storage, lbm_plan_info* out);
+
+/* Create a solver.  omega = 1/tau_0 of level 0 (viscosity nu = (1/omega - 1/2)/3,
+ * Eq. relaxationTau in lattice units); level l uses tau_l - 1/2 = 2^l (tau_0 - 1/2)
+ * (constant CFL, Section 3.2).  cs = Smagorinsky constant (Eq. eqSmago; 0 = none;
+ * ignored by FCLB).  cuda_stream = a cudaStream_t or NULL (the library then
+ * creates its own).  Every cell starts at rest (rho = 1, u = 0).
+ * On failure *out is NULL and nothing is leaked; lbm_create_error() describes it. */
+int lbm_create(lbm_ctx** out, lbm_model model, lbm_storage storage, const lbm_grid* g,
+               double omega, double cs, void* cuda_stream);
+
+/* Message of the last lbm_create failure on this thread ("" if none). */
+const char* lbm_create_error(void);
+
+/* Top-hat inflow on the face x = 0 (Section 3.2 names a constant inflow
+ * velocity; the disc and perturbation are this library's setup): ghost
+ * x = -1 holds f_eq(rho of cell x = 0, u_bc), u_bc = u_in (1 + p xi_x, p xi_y,
+ * p xi_z) where the cell centre lies within diameter/2 of (y0, z0) (coarse cell
+ * units), else 0; xi in [-1, 1) from SplitMix64 of (seed, coarse step, level,
+ * substep, y + NY_l z, component).  LBM_ERR_STATE if x is periodic. */
+int lbm_set_inflow(lbm_ctx* ctx, double y0, double z0, double diameter, double u_in,
+                   double perturb, uint64_t seed);
+
+/* f = f_eq(rho, u) on every in-domain cell of a level (host arrays: rho
+ * [NZ][NY][NX], u [3][NZ][NY][NX]; NULL = rest).  rho is the full density for
+ * both models.  Hidden cells of coarser levels are refreshed by restriction
+ * before the next step.  LBM_ERR_NONFINITE on NaN/Inf input. */
+int lbm_init_equilibrium(lbm_ctx* ctx, int level, const double* rho, const double* u);
+
+/* Per-cell body force F (host, [3][NZ][NY][NX], float64) on a single-level D3Q27
+ * grid: u = (sum f e + F/2)/rho in the collision frame and the post-collision
+ * momentum gains F.  NULL removes the force. */
+int lbm_set_force(lbm_ctx* ctx, const double* F);
+
+/* Advance coarse_steps coarse time steps (each level l takes 2^l substeps per
+ * coarse step).  Enqueues one CUDA graph per coarse step. */
+int lbm_step(lbm_ctx* ctx, int coarse_steps);
+
+/* Wait for all enqueued work; reports launch/runtime errors. */
+int lbm_sync(lbm_ctx* ctx);
+
+/* rho and u (host, float64, dense per level) of every cell that holds a value
+ * of the level (unrefined cells and hidden layers); NaN elsewhere. */
+int lbm_macroscopic(lbm_ctx* ctx, int level, double* rho, double* u);
+
+/* Float64 sums over the unrefined cells of all levels, weighted by the cell
+ * volume 8^-l: out = {sum (rho - 1), sum j_x, sum j_y, sum j_z}, j = sum f e.
+ * LBM_ERR_NONFINITE if any summed value is NaN/Inf. */
+int lbm_mass_momentum(lbm_ctx* ctx, double out[4]);
+
+/* Dense float64 copy of a level's distributions, count = Q*NX*NY*NZ doubles.
+ * Cells outside the level's blocks read NaN.  Exact for every storage. */
+int lbm_get_state(lbm_ctx* ctx, int level, double* f, size_t count);
+
+/* Inverse of lbm_get_state (rounds to the storage type).  NaN entries and
+ * cells outside the level are ignored.  Clears the pending restriction. */
+int lbm_set_state(lbm_ctx* ctx, int level, const double* f, size_t count);
+
+/* Distributions of n sampled cells (level-local dense indices) into f[n][Q]. */
+int lbm_get_cells(lbm_ctx* ctx, int level, size_t n, const int64_t* cells, double* f);
+
+/* Coarse steps taken so far (drives the inflow random numbers); settable for
+ * checkpoint/resume. */
+int lbm_get_step(const lbm_ctx* ctx, int64_t* step);
+int lbm_set_step(lbm_ctx* ctx, int64_t step);
+
+/* Kernel timing: when enabled, lbm_step launches kernels directly (no graph)
+ * between CUDA events on the context stream and accumulates per-kind device
+ * time.  kinds: 0 update (stream-collide), 1 coarse-to-fine, 2 fine-to-coarse,
+ * 3 boundary, 4 other.  ms[k] total milliseconds, launches[k] launch counts. */
+int lbm_set_profiling(lbm_ctx* ctx, int enable);
+int lbm_get_profile(lbm_ctx* ctx, double ms[5], int64_t launches[5]);
+
+/* Launch configuration of the stream-collide kernel chosen by the autotuner:
+ * threads per CTA and CTAs per launch (0 = one CTA per block). */
+int lbm_get_tuning(const lbm_ctx* ctx, int* threads, int* ctas_per_sm);
+
+/* Message describing the last failure on ctx ("" if none). */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Free everything; NULL-safe. */
+void lbm_destroy(lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

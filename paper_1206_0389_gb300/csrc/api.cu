@@ -1,0 +1,841 @@
+// C ABI of liblbm.so: context, schedule of the time-nested substeps, CUDA
+// graphs, autotuner and host <-> device staging.
+//
+// One coarse step of an L-level grid is 2^(L-1) finest substeps k.  At k the
+// levels l with k % 2^(L-1-l) == 0 take a step (level l takes 2^l per coarse
+// step, Sections 1 and 3.2); all of them run in ONE stream-collide launch,
+// preceded by the coarse-to-fine transfers into their ghost cells and their
+// boundary ghosts, and followed by the fine-to-coarse transfer of every level
+// that has just finished its second substep.  This is the same sequence of
+// values as the recursive schedule (level l, then its two fine substeps, then
+// the restriction), regrouped so independent levels share a launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "plan.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Op {
+  enum Kind { UPDATE, C2F, F2C, BC, INC } kind;
+  int level = 0;   // UPDATE: lowest level of the group; others: level concerned
+  int s = 0;       // C2F substep; BC substep index
+  UpdateArgs ua{};
+  C2FArgs ca{};
+  F2CArgs fa{};
+  BCArgs ba{};
+};
+
+struct DevLevel {
+  void* f[2] = {nullptr, nullptr};
+  void* aux[2] = {nullptr, nullptr};
+  uint8_t* kind = nullptr;
+  C2FItem* c2f = nullptr;
+  F2CItem* f2c = nullptr;
+  BCItem* bc = nullptr;
+  double* force = nullptr;
+};
+
+}  // namespace
+
+struct lbm_ctx {
+  GridPlan plan;
+  int model = 0, storage = 0, Q = 19, L = 1;
+  double omega = 1.0, cs = 0.0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0, sms = 1;
+  std::vector<DevLevel> dl;
+  WorkItem* items = nullptr;          // merged lists for each lowest level
+  std::vector<int64_t> list_off, list_len;
+  uint32_t* masks = nullptr;
+  long long* d_step = nullptr;
+  double* partial = nullptr;          // reduction scratch [L][4*sms][4]
+  double* d_out = nullptr;            // 4 doubles
+  int* d_flag = nullptr;
+  double* stage = nullptr;            // staging buffer for dense transfers
+  size_t stage_bytes = 0;
+  int parity0 = 0;                    // buffer of level 0 holding the current state
+  int64_t step = 0;
+  bool need_restrict = false;
+  bool has_force = false;
+  // inflow
+  double y0 = 0, z0 = 0, diameter = 0, u_in = 0, perturb = 0;
+  uint64_t seed = 0;
+  // launch configuration
+  int threads = 256, ctas = 0;
+  // graphs, one per level-0 parity
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  bool graphs_valid = false;
+  bool profiling = false;
+  double prof_ms[5] = {0, 0, 0, 0, 0};
+  int64_t prof_n[5] = {0, 0, 0, 0, 0};
+  std::string err;
+};
+
+namespace {
+
+int fail(lbm_ctx* c, int code, const std::string& m) {
+  if (c) c->err = m;
+  return code;
+}
+int cuda_fail(lbm_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CK(call)                                               \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+  } while (0)
+
+size_t real_bytes(int storage) { return storage == LBM_F64 ? 8 : 4; }
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& v) {
+  *dst = nullptr;
+  if (v.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(dst, v.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+void free_all(lbm_ctx* c) {
+  for (int p = 0; p < 2; ++p)
+    if (c->graph[p]) cudaGraphExecDestroy(c->graph[p]);
+  for (DevLevel& d : c->dl) {
+    cudaFree(d.f[0]);
+    cudaFree(d.f[1]);
+    cudaFree(d.aux[0]);
+    cudaFree(d.aux[1]);
+    cudaFree(d.kind);
+    cudaFree(d.c2f);
+    cudaFree(d.f2c);
+    cudaFree(d.bc);
+    cudaFree(d.force);
+  }
+  cudaFree(c->items);
+  cudaFree(c->masks);
+  cudaFree(c->d_step);
+  cudaFree(c->partial);
+  cudaFree(c->d_out);
+  cudaFree(c->d_flag);
+  cudaFree(c->stage);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+// --------------------------------------------------------------- schedule
+std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
+  std::vector<Op> ops;
+  const int L = c->L;
+  int par[kMaxL] = {0, 0, 0, 0};
+  par[0] = p0;
+  const double cs2_3 = 3.0 * c->cs * c->cs;
+  const bool les = c->model == LBM_D3Q19_MRT_LES;
+  const int K = 1 << (L - 1);
+  for (int k = 0; k < K; ++k) {
+    int lmin = L - 1;
+    for (int l = 0; l < L; ++l)
+      if (k % (1 << (L - 1 - l)) == 0) {
+        lmin = l;
+        break;
+      }
+    auto sub = [&](int l) { return k / (1 << (L - 1 - l)); };
+    for (int l = std::max(lmin, 1); l < L; ++l) {
+      const int s = sub(l) % 2;
+      const LevelPlan& fp = c->plan.lv[l];
+      const LevelPlan& cp = c->plan.lv[l - 1];
+      Op op;
+      op.kind = Op::C2F;
+      op.level = l;
+      op.s = s;
+      C2FArgs& a = op.ca;
+      a.items = c->dl[l].c2f;
+      a.n = int(fp.c2f.size());
+      const int pc = par[l - 1];
+      a.c_old = c->dl[l - 1].f[s == 0 ? pc : 1 - pc];
+      a.c_new = c->dl[l - 1].f[pc];
+      a.a_old = les ? c->dl[l - 1].aux[s == 0 ? pc : 1 - pc] : nullptr;
+      a.a_new = les ? c->dl[l - 1].aux[pc] : nullptr;
+      a.f_dst = c->dl[l].f[par[l]];
+      a.fa_dst = les ? c->dl[l].aux[par[l]] : nullptr;
+      a.s = s;
+      a.tau0_c = cp.tau0;
+      a.tau0_f = fp.tau0;
+      a.cs2_3 = cs2_3;
+      ops.push_back(op);
+    }
+    if (!c->plan.periodic_x) {
+      for (int l = lmin; l < L; ++l) {
+        const LevelPlan& lp = c->plan.lv[l];
+        Op op;
+        op.kind = Op::BC;
+        op.level = l;
+        op.s = sub(l);
+        BCArgs& b = op.ba;
+        b.items = c->dl[l].bc;
+        b.n = int(lp.bc.size());
+        b.f = c->dl[l].f[par[l]];
+        b.level = l;
+        b.substep = sub(l);
+        b.NY = lp.NY;
+        b.step = c->d_step;
+        b.y0 = c->y0;
+        b.z0 = c->z0;
+        b.r2 = (0.5 * c->diameter) * (0.5 * c->diameter);
+        b.u_in = c->u_in;
+        b.perturb = c->perturb;
+        b.inv_scale = std::ldexp(1.0, -l);
+        b.seed = c->seed;
+        ops.push_back(op);
+      }
+    }
+    Op up;
+    up.kind = Op::UPDATE;
+    up.level = lmin;
+    UpdateArgs& u = up.ua;
+    for (int l = 0; l < L; ++l) {
+      const LevelPlan& lp = c->plan.lv[l];
+      u.lv[l].src = c->dl[l].f[par[l]];
+      u.lv[l].dst = c->dl[l].f[1 - par[l]];
+      u.lv[l].aux_dst = les && L > 1 ? c->dl[l].aux[1 - par[l]] : nullptr;
+      u.lv[l].BX = lp.BX;
+      u.lv[l].BY = lp.BY;
+      u.lv[l].BZ = lp.BZ;
+      u.lv[l].tau0 = lp.tau0;
+    }
+    u.items = c->items + c->list_off[lmin];
+    u.nitems = int(c->list_len[lmin]);
+    u.masks = c->masks;
+    u.cs2_18 = 18.0 * c->cs * c->cs;
+    u.force = c->has_force ? c->dl[0].force : nullptr;
+    ops.push_back(up);
+    for (int l = lmin; l < L; ++l) par[l] ^= 1;
+    for (int l = L - 1; l >= std::max(lmin, 1); --l) {
+      if (sub(l) % 2 != 1) continue;
+      const LevelPlan& fp = c->plan.lv[l];
+      const LevelPlan& cp = c->plan.lv[l - 1];
+      Op op;
+      op.kind = Op::F2C;
+      op.level = l;
+      F2CArgs& a = op.fa;
+      a.items = c->dl[l - 1].f2c;
+      a.n = int(cp.f2c.size());
+      a.f_src = c->dl[l].f[par[l]];
+      a.fa_src = les ? c->dl[l].aux[par[l]] : nullptr;
+      a.c_dst = c->dl[l - 1].f[par[l - 1]];
+      a.ca_dst = les ? c->dl[l - 1].aux[par[l - 1]] : nullptr;
+      a.tau0_c = cp.tau0;
+      a.tau0_f = fp.tau0;
+      a.cs2_3 = cs2_3;
+      ops.push_back(op);
+    }
+  }
+  Op inc;
+  inc.kind = Op::INC;
+  ops.push_back(inc);
+  return ops;
+}
+
+cudaError_t run_op(lbm_ctx* c, const Op& op) {
+  switch (op.kind) {
+    case Op::UPDATE: return launch_update(c->model, c->storage, op.ua, c->threads, c->ctas, c->stream);
+    case Op::C2F: return launch_c2f(c->model, c->storage, op.ca, c->stream);
+    case Op::F2C: return launch_f2c(c->model, c->storage, op.fa, c->stream);
+    case Op::BC: return launch_bc(c->model, c->storage, op.ba, c->stream);
+    case Op::INC: return launch_step_inc(c->d_step, c->stream);
+  }
+  return cudaErrorInvalidValue;
+}
+
+int op_kind_index(const Op& op) {
+  switch (op.kind) {
+    case Op::UPDATE: return 0;
+    case Op::C2F: return 1;
+    case Op::F2C: return 2;
+    case Op::BC: return 3;
+    default: return 4;
+  }
+}
+
+// restriction of every hidden layer from the current fine state (after an
+// equilibrium initialisation), finest level first
+int restrict_all(lbm_ctx* ctx) {
+  const bool les = ctx->model == LBM_D3Q19_MRT_LES;
+  for (int l = ctx->L - 1; l >= 1; --l) {
+    F2CArgs a{};
+    a.items = ctx->dl[l - 1].f2c;
+    a.n = int(ctx->plan.lv[l - 1].f2c.size());
+    a.f_src = ctx->dl[l].f[0];
+    a.fa_src = les ? ctx->dl[l].aux[0] : nullptr;
+    const int pc = l - 1 == 0 ? ctx->parity0 : 0;
+    a.c_dst = ctx->dl[l - 1].f[pc];
+    a.ca_dst = les ? ctx->dl[l - 1].aux[pc] : nullptr;
+    a.tau0_c = ctx->plan.lv[l - 1].tau0;
+    a.tau0_f = ctx->plan.lv[l].tau0;
+    a.cs2_3 = 3.0 * ctx->cs * ctx->cs;
+    CK(launch_f2c(ctx->model, ctx->storage, a, ctx->stream));
+  }
+  ctx->need_restrict = false;
+  return LBM_OK;
+}
+
+int build_graphs(lbm_ctx* ctx) {
+  for (int p = 0; p < 2; ++p) {
+    if (ctx->graph[p]) {
+      cudaGraphExecDestroy(ctx->graph[p]);
+      ctx->graph[p] = nullptr;
+    }
+    std::vector<Op> ops = build_schedule(ctx, p);
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (const Op& op : ops) {
+      e = run_op(ctx, op);
+      if (e != cudaSuccess) break;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+    if (e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(ctx, e, "capture");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->graph[p], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+  }
+  ctx->graphs_valid = true;
+  return LBM_OK;
+}
+
+// Pick the stream-collide launch shape by timing the largest update launch of
+// the schedule: threads per CTA in {128, 256, 512}, one CTA per block or a
+// persistent grid of (CTAs per SM x SMs).  Writes only the other buffer.
+int autotune(lbm_ctx* ctx) {
+  const char* env = std::getenv("LBM_AUTOTUNE");
+  if (env && std::strcmp(env, "0") == 0) return LBM_OK;
+  std::vector<Op> ops = build_schedule(ctx, ctx->parity0);
+  const Op* big = nullptr;
+  for (const Op& op : ops)
+    if (op.kind == Op::UPDATE && (!big || op.ua.nitems > big->ua.nitems)) big = &op;
+  if (!big || big->ua.nitems == 0) return LBM_OK;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bt = 256, bc = 0;
+  const int tlist[3] = {128, 256, 512};
+  for (int t : tlist) {
+    int occ = 0;
+    if (update_occupancy(ctx->model, ctx->storage, t, &occ) != cudaSuccess || occ < 1) continue;
+    const int clist[2] = {0, occ * ctx->sms};
+    for (int cc : clist) {
+      if (launch_update(ctx->model, ctx->storage, big->ua, t, cc, ctx->stream) != cudaSuccess) continue;
+      CK(cudaEventRecord(e0, ctx->stream));
+      for (int r = 0; r < 3; ++r) CK(launch_update(ctx->model, ctx->storage, big->ua, t, cc, ctx->stream));
+      CK(cudaEventRecord(e1, ctx->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        bt = t;
+        bc = cc;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->threads = bt;
+  ctx->ctas = bc;
+  return LBM_OK;
+}
+
+int ensure_stage(lbm_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->stage_bytes) return LBM_OK;
+  if (ctx->stage) cudaFree(ctx->stage);
+  ctx->stage = nullptr;
+  ctx->stage_bytes = 0;
+  cudaError_t e = cudaMalloc(&ctx->stage, bytes);
+  if (e != cudaSuccess) return fail(ctx, LBM_ERR_OOM, std::string("staging buffer: ") + cudaGetErrorString(e));
+  ctx->stage_bytes = bytes;
+  return LBM_OK;
+}
+
+int cur_parity(const lbm_ctx* ctx, int level) { return level == 0 ? ctx->parity0 : 0; }
+
+// Move a dense per-level array through the device slab by slab.  hin[c] /
+// hout[c] are the host arrays of the comps components ([NZ][NY][NX] each);
+// a NULL input component is filled with fill[c] on the device.
+int slab_transfer(lbm_ctx* ctx, int level, int mode, const double* const* hin, double* const* hout,
+                  int comps, const double* fill = nullptr) {
+  const LevelPlan& lp = ctx->plan.lv[level];
+  const int64_t plane = int64_t(lp.NX) * lp.NY;
+  int nz = 8;
+  while (nz < lp.NZ && int64_t(2 * nz) * plane * comps * 8 <= (int64_t(256) << 20)) nz *= 2;
+  nz = std::min(nz, lp.NZ);
+  int rc = ensure_stage(ctx, size_t(nz) * plane * comps * sizeof(double));
+  if (rc) return rc;
+  for (int z0 = 0; z0 < lp.NZ; z0 += nz) {
+    const int n = std::min(nz, lp.NZ - z0);
+    const int64_t cnt = int64_t(n) * plane;
+    if (hin)
+      for (int c = 0; c < comps; ++c) {
+        if (hin[c])
+          CK(cudaMemcpyAsync(ctx->stage + c * cnt, hin[c] + z0 * plane, cnt * sizeof(double),
+                             cudaMemcpyHostToDevice, ctx->stream));
+        else
+          CK(launch_fill(ctx->stage + c * cnt, cnt, fill ? fill[c] : 0.0, ctx->stream));
+      }
+    SlabArgs a{};
+    a.f = ctx->dl[level].f[cur_parity(ctx, level)];
+    a.kind = ctx->dl[level].kind;
+    a.force = ctx->dl[level].force;
+    if (mode == SLAB_MACRO && !(ctx->has_force && level == 0)) a.force = nullptr;
+    a.ox = lp.ox;
+    a.oy = lp.oy;
+    a.oz = lp.oz;
+    a.BX = lp.BX;
+    a.BY = lp.BY;
+    a.BZ = lp.BZ;
+    a.NX = lp.NX;
+    a.NY = lp.NY;
+    a.z0 = z0;
+    a.nz = n;
+    a.in = ctx->stage;
+    a.out = ctx->stage;
+    a.mode = mode;
+    CK(launch_slab(ctx->model, ctx->storage, a, ctx->stream));
+    if (hout)
+      for (int c = 0; c < comps; ++c)
+        CK(cudaMemcpyAsync(hout[c] + z0 * plane, ctx->stage + c * cnt, cnt * sizeof(double),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LBM_OK;
+}
+
+bool all_finite(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+int lbm_plan(const lbm_grid* g, int model, int storage, lbm_plan_info* out) {
+  if (!g || !out) return LBM_ERR_ARG;
+  GridPlan P;
+  std::string e = build_plan(*g, model, storage, 1.0, P);
+  if (!e.empty()) return LBM_ERR_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->levels = P.levels;
+  for (int l = 0; l < P.levels; ++l) {
+    const LevelPlan& lp = P.lv[l];
+    out->blocks[l] = lp.nblocks();
+    out->level_blocks[l] = lp.level_blocks;
+    out->active_cells[l] = lp.active_cells;
+    out->updated_cells[l] = lp.updated_cells;
+    out->hidden_cells[l] = lp.hidden_cells;
+    out->ghost_cells[l] = lp.ghost_cells;
+    out->bc_cells[l] = lp.bc_cells;
+    out->updates_per_coarse_step += lp.updated_cells << l;
+    out->active_updates_per_coarse_step += lp.active_cells << l;
+  }
+  out->device_bytes = P.device_bytes;
+  return LBM_OK;
+}
+
+const char* lbm_create_error(void) { return g_create_error.c_str(); }
+
+int lbm_create(lbm_ctx** out, lbm_model model, lbm_storage storage, const lbm_grid* g, double omega,
+               double cs, void* cuda_stream) {
+  g_create_error.clear();
+  if (!out) {
+    g_create_error = "out is NULL";
+    return LBM_ERR_ARG;
+  }
+  *out = nullptr;
+  if (!g) {
+    g_create_error = "grid is NULL";
+    return LBM_ERR_ARG;
+  }
+  if (!(cs >= 0.0 && cs < 1.0)) {
+    g_create_error = "cs must be in [0, 1)";
+    return LBM_ERR_ARG;
+  }
+  lbm_ctx* ctx = new (std::nothrow) lbm_ctx();
+  if (!ctx) {
+    g_create_error = "host allocation failed";
+    return LBM_ERR_OOM;
+  }
+  std::string e = build_plan(*g, int(model), int(storage), omega, ctx->plan);
+  if (!e.empty()) {
+    g_create_error = e;
+    delete ctx;
+    return LBM_ERR_ARG;
+  }
+  ctx->model = int(model);
+  ctx->storage = int(storage);
+  ctx->Q = ctx->plan.Q;
+  ctx->L = ctx->plan.levels;
+  ctx->omega = omega;
+  ctx->cs = model == LBM_D3Q19_MRT_LES ? cs : 0.0;
+  auto bail = [&](int code, const std::string& m) {
+    g_create_error = m;
+    free_all(ctx);
+    delete ctx;
+    return code;
+  };
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev == 0)
+    return bail(LBM_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(ce));
+  cudaGetDevice(&ctx->device);
+  cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    ce = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return bail(LBM_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(ce));
+    ctx->own_stream = true;
+  }
+  const size_t sb = storage_bytes(ctx->storage), rb = real_bytes(ctx->storage);
+  const bool aux = ctx->model == LBM_D3Q19_MRT_LES && ctx->L > 1;
+  ctx->dl.resize(ctx->L);
+  std::vector<WorkItem> all;
+  std::vector<uint32_t> masks;
+  std::vector<std::vector<WorkItem>> per(ctx->L);
+  for (int l = 0; l < ctx->L; ++l) {
+    const LevelPlan& lp = ctx->plan.lv[l];
+    DevLevel& d = ctx->dl[l];
+    const size_t fb = size_t(lp.nblocks()) * 512 * ctx->Q * sb;
+    for (int p = 0; p < 2; ++p) {
+      ce = cudaMalloc(&d.f[p], fb);
+      if (ce != cudaSuccess) return bail(LBM_ERR_OOM, "distribution buffers: " + std::string(cudaGetErrorString(ce)));
+      ce = cudaMemsetAsync(d.f[p], 0, fb, ctx->stream);
+      if (ce != cudaSuccess) return bail(LBM_ERR_CUDA, cudaGetErrorString(ce));
+      if (aux) {
+        ce = cudaMalloc(&d.aux[p], size_t(lp.nblocks()) * 512 * rb);
+        if (ce != cudaSuccess) return bail(LBM_ERR_OOM, "strain buffers: " + std::string(cudaGetErrorString(ce)));
+        ce = cudaMemsetAsync(d.aux[p], 0, size_t(lp.nblocks()) * 512 * rb, ctx->stream);
+        if (ce != cudaSuccess) return bail(LBM_ERR_CUDA, cudaGetErrorString(ce));
+      }
+    }
+    if ((ce = upload(&d.kind, lp.kind)) != cudaSuccess || (ce = upload(&d.c2f, lp.c2f)) != cudaSuccess ||
+        (ce = upload(&d.f2c, lp.f2c)) != cudaSuccess || (ce = upload(&d.bc, lp.bc)) != cudaSuccess)
+      return bail(LBM_ERR_OOM, std::string("plan tables: ") + cudaGetErrorString(ce));
+    const int16_t moff = int16_t(masks.size() / 16);
+    masks.insert(masks.end(), lp.masks.begin(), lp.masks.end());
+    for (WorkItem w : lp.items) {
+      if (w.mask >= 0) w.mask = int16_t(w.mask + moff);
+      per[l].push_back(w);
+    }
+  }
+  if (masks.size() / 16 > 32767) return bail(LBM_ERR_ARG, "too many masked blocks");
+  ctx->list_off.assign(ctx->L, 0);
+  ctx->list_len.assign(ctx->L, 0);
+  for (int lmin = 0; lmin < ctx->L; ++lmin) {
+    ctx->list_off[lmin] = int64_t(all.size());
+    for (int l = lmin; l < ctx->L; ++l) all.insert(all.end(), per[l].begin(), per[l].end());
+    ctx->list_len[lmin] = int64_t(all.size()) - ctx->list_off[lmin];
+  }
+  if (all.size() > size_t(1) << 31) return bail(LBM_ERR_ARG, "too many blocks");
+  if ((ce = upload(&ctx->items, all)) != cudaSuccess || (ce = upload(&ctx->masks, masks)) != cudaSuccess)
+    return bail(LBM_ERR_OOM, std::string("work lists: ") + cudaGetErrorString(ce));
+  if ((ce = cudaMalloc(&ctx->d_step, sizeof(long long))) != cudaSuccess ||
+      (ce = cudaMemsetAsync(ctx->d_step, 0, sizeof(long long), ctx->stream)) != cudaSuccess ||
+      (ce = cudaMalloc(&ctx->partial, size_t(ctx->L) * 4 * ctx->sms * 4 * sizeof(double))) != cudaSuccess ||
+      (ce = cudaMalloc(&ctx->d_out, 4 * sizeof(double))) != cudaSuccess ||
+      (ce = cudaMalloc(&ctx->d_flag, sizeof(int))) != cudaSuccess)
+    return bail(LBM_ERR_OOM, std::string("scratch: ") + cudaGetErrorString(ce));
+  ctx->need_restrict = ctx->L > 1;
+  ce = cudaStreamSynchronize(ctx->stream);
+  if (ce != cudaSuccess) return bail(LBM_ERR_CUDA, std::string("init: ") + cudaGetErrorString(ce));
+  if (autotune(ctx) != LBM_OK) return bail(LBM_ERR_CUDA, "autotune: " + ctx->err);
+  // the tuning runs wrote the second buffers; clear them again
+  for (int l = 0; l < ctx->L; ++l) {
+    const size_t fb = size_t(ctx->plan.lv[l].nblocks()) * 512 * ctx->Q * sb;
+    cudaMemsetAsync(ctx->dl[l].f[1], 0, fb, ctx->stream);
+    if (aux) cudaMemsetAsync(ctx->dl[l].aux[1], 0, size_t(ctx->plan.lv[l].nblocks()) * 512 * rb, ctx->stream);
+  }
+  ce = cudaStreamSynchronize(ctx->stream);
+  if (ce != cudaSuccess) return bail(LBM_ERR_CUDA, std::string("init: ") + cudaGetErrorString(ce));
+  *out = ctx;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_all(ctx);
+  delete ctx;
+}
+
+const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+int lbm_set_inflow(lbm_ctx* ctx, double y0, double z0, double diameter, double u_in, double perturb,
+                   uint64_t seed) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (ctx->plan.periodic_x) return fail(ctx, LBM_ERR_STATE, "inflow needs a non-periodic x axis");
+  if (!std::isfinite(y0) || !std::isfinite(z0) || !std::isfinite(diameter) || !std::isfinite(u_in) ||
+      !std::isfinite(perturb))
+    return fail(ctx, LBM_ERR_NONFINITE, "non-finite inflow parameter");
+  if (diameter < 0 || std::fabs(u_in) >= 0.5 || perturb < 0 || perturb > 1)
+    return fail(ctx, LBM_ERR_ARG, "inflow parameters out of range");
+  ctx->y0 = y0;
+  ctx->z0 = z0;
+  ctx->diameter = diameter;
+  ctx->u_in = u_in;
+  ctx->perturb = perturb;
+  ctx->seed = seed;
+  ctx->graphs_valid = false;
+  return LBM_OK;
+}
+
+int lbm_init_equilibrium(lbm_ctx* ctx, int level, const double* rho, const double* u) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (level < 0 || level >= ctx->L) return fail(ctx, LBM_ERR_ARG, "level out of range");
+  const LevelPlan& lp = ctx->plan.lv[level];
+  const size_t n = size_t(lp.NX) * lp.NY * lp.NZ;
+  if ((rho && !all_finite(rho, n)) || (u && !all_finite(u, 3 * n)))
+    return fail(ctx, LBM_ERR_NONFINITE, "non-finite rho or u");
+  if (rho)
+    for (size_t i = 0; i < n; ++i)
+      if (!(rho[i] > 0)) return fail(ctx, LBM_ERR_ARG, "rho must be positive");
+  const double* hin[4] = {rho, u, u ? u + n : nullptr, u ? u + 2 * n : nullptr};
+  const double fill[4] = {1.0, 0.0, 0.0, 0.0};
+  int rc = slab_transfer(ctx, level, SLAB_INIT_EQ, hin, nullptr, 4, fill);
+  if (rc) return rc;
+  const bool aux = ctx->model == LBM_D3Q19_MRT_LES && ctx->L > 1;
+  if (aux)
+    for (int p = 0; p < 2; ++p)
+      CK(cudaMemsetAsync(ctx->dl[level].aux[p], 0, size_t(lp.nblocks()) * 512 * real_bytes(ctx->storage),
+                         ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->need_restrict = ctx->L > 1;
+  return LBM_OK;
+}
+
+int lbm_set_force(lbm_ctx* ctx, const double* F) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (F == nullptr) {
+    ctx->has_force = false;
+    ctx->graphs_valid = false;
+    return LBM_OK;
+  }
+  if (ctx->model != LBM_D3Q27_FCLB || ctx->L != 1)
+    return fail(ctx, LBM_ERR_STATE, "body force is defined for single-level D3Q27 grids");
+  const LevelPlan& lp = ctx->plan.lv[0];
+  const size_t n = size_t(lp.NX) * lp.NY * lp.NZ;
+  if (!all_finite(F, 3 * n)) return fail(ctx, LBM_ERR_NONFINITE, "non-finite force");
+  if (!ctx->dl[0].force) {
+    CK(cudaMalloc(&ctx->dl[0].force, size_t(lp.nblocks()) * 512 * 3 * sizeof(double)));
+    CK(cudaMemsetAsync(ctx->dl[0].force, 0, size_t(lp.nblocks()) * 512 * 3 * sizeof(double), ctx->stream));
+  }
+  const double* hin[3] = {F, F + n, F + 2 * n};
+  int rc = slab_transfer(ctx, 0, SLAB_SET_FORCE, hin, nullptr, 3);
+  if (rc) return rc;
+  ctx->has_force = true;
+  ctx->graphs_valid = false;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* ctx, int coarse_steps) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (coarse_steps < 0) return fail(ctx, LBM_ERR_ARG, "coarse_steps must be >= 0");
+  if (coarse_steps == 0) return LBM_OK;
+  if (ctx->need_restrict) {
+    int rc = restrict_all(ctx);
+    if (rc) return rc;
+  }
+  if (ctx->profiling) {
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int n = 0; n < coarse_steps; ++n) {
+      std::vector<Op> ops = build_schedule(ctx, ctx->parity0);
+      for (const Op& op : ops) {
+        CK(cudaEventRecord(e0, ctx->stream));
+        CK(run_op(ctx, op));
+        CK(cudaEventRecord(e1, ctx->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        const int k = op_kind_index(op);
+        ctx->prof_ms[k] += ms;
+        ctx->prof_n[k] += 1;
+      }
+      ctx->parity0 ^= 1;
+      ctx->step++;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return LBM_OK;
+  }
+  if (!ctx->graphs_valid) {
+    int rc = build_graphs(ctx);
+    if (rc) return rc;
+  }
+  for (int n = 0; n < coarse_steps; ++n) {
+    CK(cudaGraphLaunch(ctx->graph[ctx->parity0], ctx->stream));
+    ctx->parity0 ^= 1;
+    ctx->step++;
+  }
+  return LBM_OK;
+}
+
+int lbm_sync(lbm_ctx* ctx) {
+  if (!ctx) return LBM_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+int lbm_macroscopic(lbm_ctx* ctx, int level, double* rho, double* u) {
+  if (!ctx || !rho || !u) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+  if (level < 0 || level >= ctx->L) return fail(ctx, LBM_ERR_ARG, "level out of range");
+  const LevelPlan& lp = ctx->plan.lv[level];
+  const size_t n = size_t(lp.NX) * lp.NY * lp.NZ;
+  double* hout[4] = {rho, u, u + n, u + 2 * n};
+  return slab_transfer(ctx, level, SLAB_MACRO, nullptr, hout, 4);
+}
+
+int lbm_mass_momentum(lbm_ctx* ctx, double out[4]) {
+  if (!ctx || !out) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+  const int ctas = 4 * ctx->sms;
+  for (int l = 0; l < ctx->L; ++l) {
+    ReduceArgs a{};
+    a.f = ctx->dl[l].f[cur_parity(ctx, l)];
+    a.kind = ctx->dl[l].kind;
+    a.ncells = ctx->plan.lv[l].nblocks() * 512;
+    a.vol = std::ldexp(1.0, -3 * l);
+    a.partial = ctx->partial + size_t(l) * ctas * 4;
+    CK(launch_reduce(ctx->model, ctx->storage, a, ctas, ctx->stream));
+  }
+  CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+  CK(launch_reduce_final(ctx->partial, ctas * ctx->L, ctx->d_out, ctx->d_flag, ctx->stream));
+  int flag = 0;
+  CK(cudaMemcpyAsync(out, ctx->d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (flag) return fail(ctx, LBM_ERR_NONFINITE, "NaN or Inf in the distributions");
+  return LBM_OK;
+}
+
+int lbm_get_state(lbm_ctx* ctx, int level, double* f, size_t count) {
+  if (!ctx || !f) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+  if (level < 0 || level >= ctx->L) return fail(ctx, LBM_ERR_ARG, "level out of range");
+  const LevelPlan& lp = ctx->plan.lv[level];
+  if (count != size_t(ctx->Q) * lp.NX * lp.NY * lp.NZ) return fail(ctx, LBM_ERR_ARG, "count mismatch");
+  std::vector<double*> hout(ctx->Q);
+  const size_t n = size_t(lp.NX) * lp.NY * lp.NZ;
+  for (int i = 0; i < ctx->Q; ++i) hout[i] = f + i * n;
+  return slab_transfer(ctx, level, SLAB_GET_STATE, nullptr, hout.data(), ctx->Q);
+}
+
+int lbm_set_state(lbm_ctx* ctx, int level, const double* f, size_t count) {
+  if (!ctx || !f) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+  if (level < 0 || level >= ctx->L) return fail(ctx, LBM_ERR_ARG, "level out of range");
+  const LevelPlan& lp = ctx->plan.lv[level];
+  if (count != size_t(ctx->Q) * lp.NX * lp.NY * lp.NZ) return fail(ctx, LBM_ERR_ARG, "count mismatch");
+  for (size_t i = 0; i < count; ++i)
+    if (std::isinf(f[i])) return fail(ctx, LBM_ERR_NONFINITE, "infinite value in state");
+  std::vector<const double*> hin(ctx->Q);
+  const size_t n = size_t(lp.NX) * lp.NY * lp.NZ;
+  for (int i = 0; i < ctx->Q; ++i) hin[i] = f + i * n;
+  int rc = slab_transfer(ctx, level, SLAB_SET_STATE, hin.data(), nullptr, ctx->Q);
+  if (rc) return rc;
+  ctx->need_restrict = false;
+  return LBM_OK;
+}
+
+int lbm_get_cells(lbm_ctx* ctx, int level, size_t n, const int64_t* cells, double* f) {
+  if (!ctx || (n && (!cells || !f))) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+  if (level < 0 || level >= ctx->L) return fail(ctx, LBM_ERR_ARG, "level out of range");
+  if (n == 0) return LBM_OK;
+  const LevelPlan& lp = ctx->plan.lv[level];
+  const size_t bytes = n * sizeof(long long) + n * ctx->Q * sizeof(double);
+  int rc = ensure_stage(ctx, bytes + 16);
+  if (rc) return rc;
+  long long* dc = reinterpret_cast<long long*>(ctx->stage);
+  double* dout = ctx->stage + n;
+  CK(cudaMemcpyAsync(dc, cells, n * sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+  GatherArgs a{};
+  a.f = ctx->dl[level].f[cur_parity(ctx, level)];
+  a.ox = lp.ox;
+  a.oy = lp.oy;
+  a.oz = lp.oz;
+  a.BX = lp.BX;
+  a.BY = lp.BY;
+  a.BZ = lp.BZ;
+  a.NX = lp.NX;
+  a.NY = lp.NY;
+  a.NZ = lp.NZ;
+  a.cells = dc;
+  a.n = (long long)n;
+  a.out = dout;
+  CK(launch_gather(ctx->model, ctx->storage, a, ctx->stream));
+  CK(cudaMemcpyAsync(f, dout, n * ctx->Q * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LBM_OK;
+}
+
+int lbm_get_step(const lbm_ctx* ctx, int64_t* step) {
+  if (!ctx || !step) return LBM_ERR_ARG;
+  *step = ctx->step;
+  return LBM_OK;
+}
+
+int lbm_set_step(lbm_ctx* ctx, int64_t step) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (step < 0) return fail(ctx, LBM_ERR_ARG, "step must be >= 0");
+  long long s = step;
+  CK(cudaMemcpyAsync(ctx->d_step, &s, sizeof(s), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->step = step;
+  return LBM_OK;
+}
+
+int lbm_set_profiling(lbm_ctx* ctx, int enable) {
+  if (!ctx) return LBM_ERR_ARG;
+  ctx->profiling = enable != 0;
+  for (int k = 0; k < 5; ++k) {
+    ctx->prof_ms[k] = 0;
+    ctx->prof_n[k] = 0;
+  }
+  return LBM_OK;
+}
+
+int lbm_get_profile(lbm_ctx* ctx, double ms[5], int64_t launches[5]) {
+  if (!ctx || !ms || !launches) return LBM_ERR_ARG;
+  for (int k = 0; k < 5; ++k) {
+    ms[k] = ctx->prof_ms[k];
+    launches[k] = ctx->prof_n[k];
+  }
+  return LBM_OK;
+}
+
+int lbm_get_tuning(const lbm_ctx* ctx, int* threads, int* ctas) {
+  if (!ctx || !threads || !ctas) return LBM_ERR_ARG;
+  *threads = ctx->threads;
+  *ctas = ctx->ctas;
+  return LBM_OK;
+}
+
+}  // extern "C"

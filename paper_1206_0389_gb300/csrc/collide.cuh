@@ -1,0 +1,356 @@
+// Per-cell collision operators and equilibria (device code).
+//
+// Every function works on the shifted values g_i held in registers:
+//   D3Q19 (incompressible, Section 2): g_i = f_i, the fluctuation with sum delta rho;
+//   D3Q27 (compressible, Section 2):   g_i = f_i - w_i, with sum rho - 1.
+// Keeping the weights out of the registers keeps float32 arithmetic accurate
+// relative to the small non-equilibrium parts.
+#pragma once
+#include <cuda_fp16.h>
+
+#include "lattice.cuh"
+
+namespace lbm {
+
+// ------------------------------------------------------------------ storage
+// Storage types: double / float hold g_i; __half holds g_i / w_i.
+template <class S>
+struct Store;
+template <>
+struct Store<double> {
+  using T = double;
+  template <int Q, int i>
+  __device__ static __forceinline__ T get(const double* p) { return *p; }
+  template <int Q, int i>
+  __device__ static __forceinline__ void put(double* p, T v) { *p = v; }
+};
+template <>
+struct Store<float> {
+  using T = float;
+  template <int Q, int i>
+  __device__ static __forceinline__ T get(const float* p) { return __ldg(p); }
+  template <int Q, int i>
+  __device__ static __forceinline__ void put(float* p, T v) { *p = v; }
+};
+template <>
+struct Store<__half> {
+  using T = float;
+  template <int Q, int i>
+  __device__ static __forceinline__ T get(const __half* p) {
+    return __half2float(__ldg(p)) * float(Lattice<Q>::w(i));
+  }
+  template <int Q, int i>
+  __device__ static __forceinline__ void put(__half* p, T v) {
+    *p = __float2half_rn(v * float(1.0 / Lattice<Q>::w(i)));
+  }
+};
+
+// runtime-index variants for the small interface / utility kernels
+template <class S, int Q>
+__device__ __forceinline__ typename Store<S>::T load_rt(const S* p, int i);
+template <class S, int Q>
+__device__ __forceinline__ void store_rt(S* p, int i, typename Store<S>::T v);
+
+template <int Q>
+__device__ __forceinline__ double weight_rt(int i) {
+  double w = 0.0;
+  static_for<Q>([&](auto c) {
+    if (i == c) w = Lattice<Q>::w(c);
+  });
+  return w;
+}
+
+template <>
+__device__ __forceinline__ double load_rt<double, 19>(const double* p, int) { return *p; }
+template <>
+__device__ __forceinline__ double load_rt<double, 27>(const double* p, int) { return *p; }
+template <>
+__device__ __forceinline__ float load_rt<float, 19>(const float* p, int) { return *p; }
+template <>
+__device__ __forceinline__ float load_rt<float, 27>(const float* p, int) { return *p; }
+template <>
+__device__ __forceinline__ float load_rt<__half, 19>(const __half* p, int i) {
+  return __half2float(*p) * float(weight_rt<19>(i));
+}
+template <>
+__device__ __forceinline__ float load_rt<__half, 27>(const __half* p, int i) {
+  return __half2float(*p) * float(weight_rt<27>(i));
+}
+template <>
+__device__ __forceinline__ void store_rt<double, 19>(double* p, int, double v) { *p = v; }
+template <>
+__device__ __forceinline__ void store_rt<double, 27>(double* p, int, double v) { *p = v; }
+template <>
+__device__ __forceinline__ void store_rt<float, 19>(float* p, int, float v) { *p = v; }
+template <>
+__device__ __forceinline__ void store_rt<float, 27>(float* p, int, float v) { *p = v; }
+template <>
+__device__ __forceinline__ void store_rt<__half, 19>(__half* p, int i, float v) {
+  *p = __float2half_rn(v / float(weight_rt<19>(i)));
+}
+template <>
+__device__ __forceinline__ void store_rt<__half, 27>(__half* p, int i, float v) {
+  *p = __float2half_rn(v / float(weight_rt<27>(i)));
+}
+
+// ------------------------------------------------------------------ D3Q19 MRT-LES
+// Incompressible equilibrium (Section 2, c = 1): w (drho + 3 e.u + 9/2 (e.u)^2 - 3/2 u^2).
+template <class T>
+__device__ __forceinline__ void feq19(T drho, T ux, T uy, T uz, T* out) {
+  const T uu = T(1.5) * (ux * ux + uy * uy + uz * uz);
+  static_for<19>([&](auto i) {
+    constexpr int x = D3Q19::ex(i), y = D3Q19::ey(i), z = D3Q19::ez(i);
+    const T eu = T(x) * ux + T(y) * uy + T(z) * uz;
+    out[i] = T(D3Q19::w(i)) * (drho + T(3) * eu + T(4.5) * eu * eu - uu);
+  });
+}
+
+template <class T>
+__device__ __forceinline__ void moments19(const T* g, T& drho, T& ux, T& uy, T& uz) {
+  drho = T(0);
+  ux = uy = uz = T(0);
+  static_for<19>([&](auto i) {
+    drho += g[i];
+    if constexpr (D3Q19::ex(i) != 0) ux += T(D3Q19::ex(i)) * g[i];
+    if constexpr (D3Q19::ey(i) != 0) uy += T(D3Q19::ey(i)) * g[i];
+    if constexpr (D3Q19::ez(i) != 0) uz += T(D3Q19::ez(i)) * g[i];
+  });
+}
+
+// MRT with every non-shear rate 1 (the paper's choice, Section 2) written in
+// closed form: f* = f_eq + (1 - s1) P (f - f_eq).  P keeps the five shear
+// moments of Table 1 (s1 group) of the non-equilibrium part and drops all
+// others: axis links receive 1/2 (Pi_aa - tr Pi / 3), the diagonal links of
+// plane ab receive 1/4 e_a e_b Pi_ab, the rest link 0.  s1 = 1/tau_total with
+// tau_total from Eq. eqTauTotFinal and Q from Eq. EqnQ.
+// Returns |S| = 3 Q / (2 tau_total) (Eq. eqStrainRate, lattice units).
+template <class T>
+__device__ __forceinline__ T collide19(T* g, T tau0, T cs2_18) {
+  T drho, ux, uy, uz;
+  moments19(g, drho, ux, uy, uz);
+  T feq[19];
+  feq19(drho, ux, uy, uz, feq);
+  T pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+  static_for<19>([&](auto i) {
+    constexpr int x = D3Q19::ex(i), y = D3Q19::ey(i), z = D3Q19::ez(i);
+    const T n = g[i] - feq[i];
+    g[i] = n;  // keep the non-equilibrium part
+    if constexpr (x != 0) pxx += n;
+    if constexpr (y != 0) pyy += n;
+    if constexpr (z != 0) pzz += n;
+    if constexpr (x * y != 0) pxy += T(x * y) * n;
+    if constexpr (x * z != 0) pxz += T(x * z) * n;
+    if constexpr (y * z != 0) pyz += T(y * z) * n;
+  });
+  const T qq = T(2) * (pxx * pxx + pyy * pyy + pzz * pzz +
+                       T(2) * (pxy * pxy + pxz * pxz + pyz * pyz));
+  const T Qn = sqrt(qq);
+  const T tau = T(0.5) * (tau0 + sqrt(tau0 * tau0 + cs2_18 * Qn));
+  const T k = T(1) - T(1) / tau;
+  const T tr3 = (pxx + pyy + pzz) * T(1.0 / 3.0);
+  const T ax = T(0.5) * k * (pxx - tr3), ay = T(0.5) * k * (pyy - tr3), az = T(0.5) * k * (pzz - tr3);
+  const T dxy = T(0.25) * k * pxy, dxz = T(0.25) * k * pxz, dyz = T(0.25) * k * pyz;
+  static_for<19>([&](auto i) {
+    constexpr int x = D3Q19::ex(i), y = D3Q19::ey(i), z = D3Q19::ez(i);
+    constexpr int nz = (x != 0) + (y != 0) + (z != 0);
+    T p = T(0);
+    if constexpr (nz == 1) p = (x != 0) ? ax : (y != 0) ? ay : az;
+    if constexpr (nz == 2) {
+      if constexpr (z == 0) p = T(x * y) * dxy;
+      else if constexpr (y == 0) p = T(x * z) * dxz;
+      else p = T(y * z) * dyz;
+    }
+    g[i] = feq[i] + p;
+  });
+  return T(1.5) * Qn / tau;
+}
+
+// ------------------------------------------------------------------ D3Q27 FCLB
+// Central moments by three one-dimensional passes (z, then y, then x): the
+// D3Q27 velocity set is the product {-1,0,1}^3 and the central-moment
+// matrix of Section 2 factorises into 3x3 per-axis transforms.  Each pass is
+// written for deviations from the weight part: a line whose weight part is
+// K (w1(-1), w1(0), w1(+1)) = K (1/6, 2/3, 1/6) has moments K (1, 0, 1/3) at
+// rest, and the pass outputs the deviations from those.  After three passes
+// v[a][b][c] = rho kappa_abc - C_abc with C_abc = c_a c_b c_c, c = (1, 0, 1/3).
+// (Index 0/1/2 means velocity -1/0/+1 before a pass and order 0/1/2 after.)
+__host__ __device__ constexpr double w1(int k) { return k == 1 ? 2.0 / 3.0 : 1.0 / 6.0; }
+__host__ __device__ constexpr double c1(int k) { return k == 0 ? 1.0 : k == 1 ? 0.0 : 1.0 / 3.0; }
+
+template <class T>
+__device__ __forceinline__ void fwd_line(T& a, T& b, T& c, T u, T uu, T K) {
+  const T m0 = a + b + c;
+  const T d = c - a;
+  const T s = c + a;
+  const T m0k = m0 + K;
+  a = m0;
+  b = d - u * m0k;
+  c = s - T(2) * u * d + uu * m0k;
+}
+template <class T>
+__device__ __forceinline__ void inv_line(T& a, T& b, T& c, T u, T uu, T K) {
+  const T m0 = a, m1 = b, m2 = c;
+  const T m0k = m0 + K;
+  const T gm = T(0.5) * ((uu - u) * m0k + (T(2) * u - T(1)) * m1 + m2);
+  const T gp = T(0.5) * ((uu + u) * m0k + (T(2) * u + T(1)) * m1 + m2);
+  const T g0 = m0 * (T(1) - uu) - T(2) * u * m1 - m2 - K * uu;
+  a = gm;
+  b = g0;
+  c = gp;
+}
+
+template <class T>
+__device__ __forceinline__ void forward27(T (&v)[3][3][3], T ux, T uy, T uz) {
+  const T ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) fwd_line(v[i][j][0], v[i][j][1], v[i][j][2], uz, uz2, T(w1(i) * w1(j)));
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) fwd_line(v[i][0][k], v[i][1][k], v[i][2][k], uy, uy2, T(w1(i) * c1(k)));
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) fwd_line(v[0][j][k], v[1][j][k], v[2][j][k], ux, ux2, T(c1(j) * c1(k)));
+}
+
+template <class T>
+__device__ __forceinline__ void inverse27(T (&v)[3][3][3], T ux, T uy, T uz) {
+  const T ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) inv_line(v[0][j][k], v[1][j][k], v[2][j][k], ux, ux2, T(c1(j) * c1(k)));
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) inv_line(v[i][0][k], v[i][1][k], v[i][2][k], uy, uy2, T(w1(i) * c1(k)));
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) inv_line(v[i][j][0], v[i][j][1], v[i][j][2], uz, uz2, T(w1(i) * w1(j)));
+}
+
+template <class T>
+__device__ __forceinline__ void to_cube(const T* g, T (&v)[3][3][3]) {
+  static_for<27>([&](auto i) { v[D3Q27::ex(i) + 1][D3Q27::ey(i) + 1][D3Q27::ez(i) + 1] = g[i]; });
+}
+template <class T>
+__device__ __forceinline__ void from_cube(const T (&v)[3][3][3], T* g) {
+  static_for<27>([&](auto i) { g[i] = v[D3Q27::ex(i) + 1][D3Q27::ey(i) + 1][D3Q27::ez(i) + 1]; });
+}
+
+template <class T>
+__device__ __forceinline__ void moments27(const T* g, T& drho, T& jx, T& jy, T& jz) {
+  drho = jx = jy = jz = T(0);
+  static_for<27>([&](auto i) {
+    drho += g[i];
+    if constexpr (D3Q27::ex(i) != 0) jx += T(D3Q27::ex(i)) * g[i];
+    if constexpr (D3Q27::ey(i) != 0) jy += T(D3Q27::ey(i)) * g[i];
+    if constexpr (D3Q27::ez(i) != 0) jz += T(D3Q27::ez(i)) * g[i];
+  });
+}
+
+// Factorized cascaded collision (Section 2, Table 2; whole moments recomputed):
+// the normal-stress differences and shear moments relax with omega, the
+// trace and every higher moment with rate 1 to the Table 2 equilibria built
+// from the post-collision second-order moments (third and fifth order 0,
+// fourth M_aa M_bb and M_aa M_bc, sixth M11 M22 M33).  With a body force F,
+// u = (j + F/2)/rho and the first central moments leave as F/(2 rho).
+template <class T>
+__device__ __forceinline__ void collide27(T* g, T omega, T Fx, T Fy, T Fz) {
+  T drho, jx, jy, jz;
+  moments27(g, drho, jx, jy, jz);
+  const T rho = T(1) + drho;
+  const T irho = T(1) / rho;
+  const T ux = (jx + T(0.5) * Fx) * irho, uy = (jy + T(0.5) * Fy) * irho, uz = (jz + T(0.5) * Fz) * irho;
+  T v[3][3][3];
+  to_cube(g, v);
+  forward27(v, ux, uy, uz);
+  const T om1 = T(1) - omega;
+  const T mean = (v[2][0][0] + v[0][2][0] + v[0][0][2]) * T(1.0 / 3.0);
+  const T Dx = om1 * (v[2][0][0] - mean) * irho;
+  const T Dy = om1 * (v[0][2][0] - mean) * irho;
+  const T Dz = om1 * (v[0][0][2] - mean) * irho;
+  const T kxy = om1 * v[1][1][0], kxz = om1 * v[1][0][1], kyz = om1 * v[0][1][1];  // rho kappa'
+  const T third = T(1.0 / 3.0);
+  const T Xx = third + Dx, Yy = third + Dy, Zz = third + Dz;  // kappa'_200 ...
+  // zeroth and first order
+  v[0][0][0] = drho;
+  v[1][0][0] = T(0.5) * Fx;
+  v[0][1][0] = T(0.5) * Fy;
+  v[0][0][1] = T(0.5) * Fz;
+  // second order
+  v[2][0][0] = drho * third + rho * Dx;
+  v[0][2][0] = drho * third + rho * Dy;
+  v[0][0][2] = drho * third + rho * Dz;
+  v[1][1][0] = kxy;
+  v[1][0][1] = kxz;
+  v[0][1][1] = kyz;
+  // third order
+  v[2][1][0] = v[2][0][1] = v[1][2][0] = v[0][2][1] = v[1][0][2] = v[0][1][2] = v[1][1][1] = T(0);
+  // fourth order
+  const T ninth = T(1.0 / 9.0);
+  v[2][2][0] = drho * ninth + rho * ((Dx + Dy) * third + Dx * Dy);
+  v[2][0][2] = drho * ninth + rho * ((Dx + Dz) * third + Dx * Dz);
+  v[0][2][2] = drho * ninth + rho * ((Dy + Dz) * third + Dy * Dz);
+  v[2][1][1] = Xx * kyz;
+  v[1][2][1] = Yy * kxz;
+  v[1][1][2] = Zz * kxy;
+  // fifth order
+  v[2][2][1] = v[2][1][2] = v[1][2][2] = T(0);
+  // sixth order
+  v[2][2][2] = drho * T(1.0 / 27.0) +
+               rho * ((Dx + Dy + Dz) * ninth + (Dx * Dy + Dx * Dz + Dy * Dz) * third + Dx * Dy * Dz);
+  inverse27(v, ux, uy, uz);
+  from_cube(v, g);
+}
+
+// Product-form D3Q27 equilibrium minus the weights: the distribution whose
+// normalised central moments are the Table 2 equilibria at rest shape.  Built
+// with the same inverse transform from the deviations drho * C_abc.
+template <class T>
+__device__ __forceinline__ void feq27(T drho, T ux, T uy, T uz, T* out) {
+  T v[3][3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) v[a][b][c] = drho * T(c1(a) * c1(b) * c1(c));
+  inverse27(v, ux, uy, uz);
+  from_cube(v, out);
+}
+
+// ------------------------------------------------------------------ model traits
+struct MrtLes {
+  static constexpr int Q = 19;
+  template <class T>
+  __device__ static __forceinline__ void moments(const T* g, T& rl, T& ux, T& uy, T& uz) {
+    moments19(g, rl, ux, uy, uz);  // rho_0 = 1
+  }
+  template <class T>
+  __device__ static __forceinline__ void feq(T rl, T ux, T uy, T uz, T* out) {
+    feq19(rl, ux, uy, uz, out);
+  }
+};
+struct Fclb {
+  static constexpr int Q = 27;
+  template <class T>
+  __device__ static __forceinline__ void moments(const T* g, T& rl, T& ux, T& uy, T& uz) {
+    T jx, jy, jz;
+    moments27(g, rl, jx, jy, jz);
+    const T ir = T(1) / (T(1) + rl);
+    ux = jx * ir;
+    uy = jy * ir;
+    uz = jz * ir;
+  }
+  template <class T>
+  __device__ static __forceinline__ void feq(T rl, T ux, T uy, T uz, T* out) {
+    feq27(rl, ux, uy, uz, out);
+  }
+};
+
+}  // namespace lbm

@@ -1,0 +1,203 @@
+// Level-interface and boundary kernels of the time-nested grid.
+//
+// Coarse-to-fine (Yu et al., cited in Sections 1 and 3.2; reading fixed by
+// this library): each fine ghost cell receives the trilinear interpolation F^
+// of the coarse post-collision values (at t for fine substep 0, the mean of t
+// and t+1 for substep 1), then f~_f = f_eq(F^) + r_cf (F^ - f_eq(F^)),
+// r_cf = (tau_f - 1) / (2 (tau_c - 1)), with the Smagorinsky |S| carried by
+// the same interpolation (tau_c = tau0_c + 3 Cs^2 |S|, tau_f = tau0_f + 3 Cs^2 |S|/2).
+// Fine-to-coarse: hidden coarse cells take the mean over their 8 children of
+// f_eq + r_fc (f~ - f_eq), r_fc = 2 (tau_c - 1) / (tau_f - 1), with tau_f the
+// child's own and tau_c = tau0_c + 3 Cs^2 (2 |S|_child).
+// Boundaries: inflow ghost = f_eq(rho of the adjacent cell, u_bc) with the
+// top-hat disc velocity (Section 3.2 names a constant inflow velocity); outflow
+// ghost = copy of the adjacent cell (zero gradient).
+#include "collide.cuh"
+#include "kernels.cuh"
+
+namespace lbm {
+
+template <class M, class S>
+__global__ void k_c2f(const C2FArgs a) {
+  using St = Store<S>;
+  using T = typename St::T;
+  constexpr int Q = M::Q;
+  constexpr int QS = Q * kCells;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.n) return;
+  const C2FItem it = a.items[n];
+  const T tx = (it.tbits & 1) ? T(0.75) : T(0.25);
+  const T ty = (it.tbits & 2) ? T(0.75) : T(0.25);
+  const T tz = (it.tbits & 4) ? T(0.75) : T(0.25);
+  T F[Q];
+  static_for<Q>([&](auto i) { F[i] = T(0); });
+  T Sh = T(0);
+  const S* co = reinterpret_cast<const S*>(a.c_old);
+  const S* cn = reinterpret_cast<const S*>(a.c_new);
+#pragma unroll 1
+  for (int k = 0; k < 8; ++k) {
+    const T wx = (k & 1) ? tx : T(1) - tx;
+    const T wy = (k & 2) ? ty : T(1) - ty;
+    const T wz = (k & 4) ? tz : T(1) - tz;
+    const T W = wz * wy * wx;
+    const int64_t base = int64_t(it.cblock[k]) * QS + it.ccell[k];
+    static_for<Q>([&](auto i) {
+      T v = St::template get<Q, i>(co + base + int(i) * kCells);
+      if (a.s == 1) v = T(0.5) * (v + St::template get<Q, i>(cn + base + int(i) * kCells));
+      F[i] += W * v;
+    });
+    if (a.a_old != nullptr) {
+      const int64_t j = int64_t(it.cblock[k]) * kCells + it.ccell[k];
+      T sv = reinterpret_cast<const T*>(a.a_old)[j];
+      if (a.s == 1) sv = T(0.5) * (sv + reinterpret_cast<const T*>(a.a_new)[j]);
+      Sh += W * sv;
+    }
+  }
+  T rl, ux, uy, uz;
+  M::moments(F, rl, ux, uy, uz);
+  T feq[Q];
+  M::feq(rl, ux, uy, uz, feq);
+  const T tc = T(a.tau0_c) + T(a.cs2_3) * Sh;
+  const T tf = T(a.tau0_f) + T(a.cs2_3) * Sh / T(2);
+  const T r = (tf - T(1)) / (T(2) * (tc - T(1)));
+  S* fd = reinterpret_cast<S*>(a.f_dst) + int64_t(it.fblock) * QS + it.fcell;
+  static_for<Q>([&](auto i) { St::template put<Q, i>(fd + int(i) * kCells, feq[i] + r * (F[i] - feq[i])); });
+  if (a.fa_dst != nullptr) reinterpret_cast<T*>(a.fa_dst)[int64_t(it.fblock) * kCells + it.fcell] = Sh / T(2);
+}
+
+template <class M, class S>
+__global__ void k_f2c(const F2CArgs a) {
+  using St = Store<S>;
+  using T = typename St::T;
+  constexpr int Q = M::Q;
+  constexpr int QS = Q * kCells;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.n) return;
+  const F2CItem it = a.items[n];
+  const S* fs = reinterpret_cast<const S*>(a.f_src);
+  T acc[Q];
+  static_for<Q>([&](auto i) { acc[i] = T(0); });
+  T accS = T(0);
+#pragma unroll 1
+  for (int ch = 0; ch < 8; ++ch) {
+    const int64_t base = int64_t(it.fblock[ch]) * QS + it.fcell[ch];
+    T g[Q];
+    static_for<Q>([&](auto i) { g[i] = St::template get<Q, i>(fs + base + int(i) * kCells); });
+    T Sk = T(0);
+    if (a.fa_src != nullptr) Sk = reinterpret_cast<const T*>(a.fa_src)[int64_t(it.fblock[ch]) * kCells + it.fcell[ch]];
+    T rl, ux, uy, uz;
+    M::moments(g, rl, ux, uy, uz);
+    T feq[Q];
+    M::feq(rl, ux, uy, uz, feq);
+    const T tf = T(a.tau0_f) + T(a.cs2_3) * Sk;
+    const T tc = T(a.tau0_c) + T(a.cs2_3) * T(2) * Sk;
+    const T r = T(2) * (tc - T(1)) / (tf - T(1));
+    static_for<Q>([&](auto i) { acc[i] += feq[i] + r * (g[i] - feq[i]); });
+    accS += T(2) * Sk;
+  }
+  S* cd = reinterpret_cast<S*>(a.c_dst) + int64_t(it.cblock) * QS + it.ccell;
+  static_for<Q>([&](auto i) { St::template put<Q, i>(cd + int(i) * kCells, acc[i] / T(8)); });
+  if (a.ca_dst != nullptr) reinterpret_cast<T*>(a.ca_dst)[int64_t(it.cblock) * kCells + it.ccell] = accS / T(8);
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): advance by the golden gamma, then mix.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// xi in [-1, 1) for one boundary value: chain over (seed, coarse step,
+// level << 32 | substep, cell, component)
+__device__ __forceinline__ double inflow_xi(unsigned long long seed, long long step, int level,
+                                            int substep, long long cell, int comp) {
+  unsigned long long h = splitmix64(seed);
+  h = splitmix64(h ^ (unsigned long long)step);
+  h = splitmix64(h ^ (((unsigned long long)level << 32) | (unsigned long long)substep));
+  h = splitmix64(h ^ (unsigned long long)cell);
+  h = splitmix64(h ^ (unsigned long long)comp);
+  return 2.0 * double(h >> 11) * 0x1.0p-53 - 1.0;
+}
+
+template <class M, class S>
+__global__ void k_bc(const BCArgs a) {
+  using St = Store<S>;
+  using T = typename St::T;
+  constexpr int Q = M::Q;
+  constexpr int QS = Q * kCells;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.n) return;
+  const BCItem it = a.items[n];
+  S* f = reinterpret_cast<S*>(a.f);
+  const S* src = f + int64_t(it.sblock) * QS + it.scell;
+  S* dst = f + int64_t(it.gblock) * QS + it.gcell;
+  if (it.type == 1) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dst[i * kCells] = src[i * kCells];
+    return;
+  }
+  T g[Q];
+  static_for<Q>([&](auto i) { g[i] = St::template get<Q, i>(src + int(i) * kCells); });
+  T rl = T(0);
+  static_for<Q>([&](auto i) { rl += g[i]; });
+  const double yc = (double(it.y) + 0.5) * a.inv_scale;
+  const double zc = (double(it.z) + 0.5) * a.inv_scale;
+  const double dy = yc - a.y0, dz = zc - a.z0;
+  double ux = 0.0, uy = 0.0, uz = 0.0;
+  if (dy * dy + dz * dz < a.r2) {
+    const long long step = *a.step;
+    const long long cell = (long long)it.y + (long long)a.NY * it.z;
+    const double xx = inflow_xi(a.seed, step, a.level, a.substep, cell, 0);
+    const double xy = inflow_xi(a.seed, step, a.level, a.substep, cell, 1);
+    const double xz = inflow_xi(a.seed, step, a.level, a.substep, cell, 2);
+    ux = a.u_in * (1.0 + a.perturb * xx);
+    uy = a.u_in * a.perturb * xy;
+    uz = a.u_in * a.perturb * xz;
+  }
+  T feq[Q];
+  M::feq(rl, T(ux), T(uy), T(uz), feq);
+  static_for<Q>([&](auto i) { St::template put<Q, i>(dst + int(i) * kCells, feq[i]); });
+}
+
+__global__ void k_step_inc(long long* step) { *step += 1; }
+
+template <class M, class S>
+static cudaError_t c2f_ms(const C2FArgs& a, cudaStream_t st) {
+  if (a.n == 0) return cudaSuccess;
+  k_c2f<M, S><<<(a.n + 127) / 128, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+template <class M, class S>
+static cudaError_t f2c_ms(const F2CArgs& a, cudaStream_t st) {
+  if (a.n == 0) return cudaSuccess;
+  k_f2c<M, S><<<(a.n + 127) / 128, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+template <class M, class S>
+static cudaError_t bc_ms(const BCArgs& a, cudaStream_t st) {
+  if (a.n == 0) return cudaSuccess;
+  k_bc<M, S><<<(a.n + 127) / 128, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+#define LBM_DISPATCH(FN, ...)                                              \
+  if (model == LBM_D3Q19_MRT_LES) {                                        \
+    if (storage == LBM_F64) return FN<MrtLes, double>(__VA_ARGS__);        \
+    if (storage == LBM_F32) return FN<MrtLes, float>(__VA_ARGS__);         \
+    return FN<MrtLes, __half>(__VA_ARGS__);                                \
+  }                                                                        \
+  if (storage == LBM_F64) return FN<Fclb, double>(__VA_ARGS__);            \
+  if (storage == LBM_F32) return FN<Fclb, float>(__VA_ARGS__);             \
+  return FN<Fclb, __half>(__VA_ARGS__);
+
+cudaError_t launch_c2f(int model, int storage, const C2FArgs& a, cudaStream_t st) { LBM_DISPATCH(c2f_ms, a, st) }
+cudaError_t launch_f2c(int model, int storage, const F2CArgs& a, cudaStream_t st) { LBM_DISPATCH(f2c_ms, a, st) }
+cudaError_t launch_bc(int model, int storage, const BCArgs& a, cudaStream_t st) { LBM_DISPATCH(bc_ms, a, st) }
+
+cudaError_t launch_step_inc(long long* step, cudaStream_t st) {
+  k_step_inc<<<1, 1, 0, st>>>(step);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

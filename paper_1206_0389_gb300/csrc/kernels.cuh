@@ -1,0 +1,164 @@
+// Launch-parameter structures shared by the host side and the kernels, and
+// the host-callable launchers (implemented in the .cu files).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+constexpr int kCells = 512;  // cells per 8^3 block, index x + 8 y + 64 z
+constexpr int kMaxL = LBM_MAX_LEVELS;
+
+// one unit of stream-collide work: a block of one level, optionally masked.
+// edges: bit 2a (2a+1) set when the block sits on the low (high) face of a
+// level box that wraps periodically along axis a (x, y, z).
+struct WorkItem {
+  int32_t block;
+  uint8_t level;
+  uint8_t edges;
+  int16_t mask;  // -1: all 512 cells; else index into the mask table
+};
+
+// cell kinds kept per level on the device (for outputs and audits)
+enum CellKind : uint8_t {
+  K_NONE = 0,     // allocated but holds no value of the level
+  K_ACTIVE = 1,   // unrefined cell of the level
+  K_HIDDEN1 = 2,  // refined, Chebyshev distance 1 from an active cell
+  K_HIDDEN2 = 3,  // refined, distance 2
+  K_REFINED = 4,  // refined, deeper inside
+  K_GHOST = 5,    // coarse-to-fine ghost cell
+  K_BC = 6        // inflow/outflow ghost cell
+};
+
+struct LevelPtrs {
+  const void* src;    // storage [nblocks][Q][512], nblocks = BX*BY*BZ
+  void* dst;
+  void* aux_dst;      // |S| per cell [nblocks][512] (real) or nullptr
+  int BX, BY, BZ;     // level box in blocks
+  double tau0;
+};
+
+struct UpdateArgs {
+  LevelPtrs lv[kMaxL];
+  const WorkItem* items;
+  int nitems;
+  const uint32_t* masks;  // 16 words per mask
+  double cs2_18;          // 18 Cs^2
+  const double* force;    // level 0 body force [3][nblocks*512] (block order) or nullptr
+};
+
+// coarse-to-fine: one fine ghost cell and its 8 coarse stencil cells
+struct C2FItem {
+  int32_t fblock;
+  int16_t fcell;
+  uint8_t tbits;  // bit a: weight of the upper coarse index along axis a is 3/4 (else 1/4)
+  uint8_t pad;
+  int32_t cblock[8];  // order (dz, dy, dx) with dx fastest; 0 = lower, 1 = upper index
+  int16_t ccell[8];
+};
+
+// fine-to-coarse: one hidden coarse cell and its 8 children (dz, dy, dx order)
+struct F2CItem {
+  int32_t cblock;
+  int16_t ccell;
+  int16_t pad;
+  int32_t fblock[8];
+  int16_t fcell[8];
+};
+
+// boundary ghost cell
+struct BCItem {
+  int32_t gblock;
+  int16_t gcell;
+  int8_t type;  // 0 inflow (x = -1), 1 outflow (x = NX)
+  int8_t pad;
+  int32_t sblock;
+  int16_t scell;
+  int16_t pad2;
+  int32_t y, z;  // level-local cell coordinates of the face cell
+};
+
+struct C2FArgs {
+  const C2FItem* items;
+  int n;
+  const void* c_old;  // coarse storage at t
+  const void* c_new;  // coarse storage at t+1 (used when s == 1)
+  const void* a_old;  // coarse |S| at t (LES) or nullptr
+  const void* a_new;
+  void* f_dst;        // fine storage receiving the ghost values
+  void* fa_dst;       // fine |S| (LES) or nullptr
+  int s;              // fine substep 0 or 1
+  double tau0_c, tau0_f, cs2_3;  // cs2_3 = 3 Cs^2
+};
+
+struct F2CArgs {
+  const F2CItem* items;
+  int n;
+  const void* f_src;  // fine storage at t+1
+  const void* fa_src;
+  void* c_dst;        // coarse storage at t+1
+  void* ca_dst;
+  double tau0_c, tau0_f, cs2_3;
+};
+
+struct BCArgs {
+  const BCItem* items;
+  int n;
+  void* f;  // level storage at the current time (ghosts written in place)
+  int level, substep, NY;
+  const long long* step;  // device coarse-step counter
+  double y0, z0, r2, u_in, perturb, inv_scale;  // inv_scale = 2^-level
+  unsigned long long seed;
+};
+
+// ------------------------------------------------------------------ launchers
+// model: 0 D3Q19 MRT-LES, 1 D3Q27 FCLB; storage: lbm_storage.
+cudaError_t launch_update(int model, int storage, const UpdateArgs& a, int threads, int ctas,
+                          cudaStream_t st);
+cudaError_t update_occupancy(int model, int storage, int threads, int* ctas_per_sm);
+cudaError_t launch_c2f(int model, int storage, const C2FArgs& a, cudaStream_t st);
+cudaError_t launch_f2c(int model, int storage, const F2CArgs& a, cudaStream_t st);
+cudaError_t launch_bc(int model, int storage, const BCArgs& a, cudaStream_t st);
+cudaError_t launch_step_inc(long long* step, cudaStream_t st);
+
+// dense <-> block staging for one slab of cell layers [z0, z0 + nz) of a level
+enum SlabMode { SLAB_SET_STATE = 0, SLAB_GET_STATE = 1, SLAB_INIT_EQ = 2, SLAB_MACRO = 3,
+                SLAB_SET_FORCE = 4 };
+struct SlabArgs {
+  void* f;                // level storage (current buffer)
+  const uint8_t* kind;    // [nblocks][512] cell kinds
+  double* force;          // level body force [3][nblocks*512] or nullptr
+  int ox, oy, oz, BX, BY, BZ;  // level box
+  int NX, NY, z0, nz;
+  const double* in;       // SET_STATE: f [Q][n]; INIT_EQ: rho [n], u [3][n]; SET_FORCE: F [3][n]
+  double* out;            // GET_STATE: f [Q][n]; MACRO: rho [n], u [3][n]
+  int mode;
+};
+cudaError_t launch_slab(int model, int storage, const SlabArgs& a, cudaStream_t st);
+cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t st);
+
+struct GatherArgs {
+  const void* f;
+  int ox, oy, oz, BX, BY, BZ;
+  int NX, NY, NZ;
+  const long long* cells;
+  long long n;
+  double* out;  // [n][Q]
+};
+cudaError_t launch_gather(int model, int storage, const GatherArgs& a, cudaStream_t st);
+
+struct ReduceArgs {
+  const void* f;
+  const uint8_t* kind;
+  long long ncells;  // nblocks * 512
+  double vol;
+  double* partial;   // [gridDim][4]
+};
+cudaError_t launch_reduce(int model, int storage, const ReduceArgs& a, int ctas, cudaStream_t st);
+cudaError_t launch_reduce_final(const double* partial, int n, double* out, int* nonfinite,
+                                cudaStream_t st);
+
+}  // namespace lbm

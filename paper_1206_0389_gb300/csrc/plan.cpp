@@ -1,0 +1,445 @@
+// Host-side grid planner: levels, dense level boxes, cell kinds and the work
+// lists of the stream-collide, interface and boundary kernels.  Pure C++.
+//
+// Reading of the interface scheme of Yu et al. (cited in Sections 1 and 3.2
+// of the paper, which do not write it out), cell-centred 2:1:
+//   active   cells of unrefined blocks of the level;
+//   hidden 1 / hidden 2: refined cells at Chebyshev distance 1 / 2 from an
+//            active cell; they receive the fine-to-coarse transfer, and
+//            hidden 1 is also streamed and collided on the coarse level so the
+//            coarse-to-fine temporal interpolation has a value at t+1;
+//   ghost    cells outside the level's blocks at distance 1 from them; they
+//            receive the coarse-to-fine transfer before every substep.
+#include "plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+namespace lbm {
+
+size_t storage_bytes(int st) { return st == LBM_F64 ? 8 : st == LBM_F32 ? 4 : 2; }
+
+int32_t LevelPlan::box_id(int bx, int by, int bz) const {
+  const int X = bx - ox, Y = by - oy, Z = bz - oz;
+  if (X < 0 || X >= BX || Y < 0 || Y >= BY || Z < 0 || Z >= BZ) return -1;
+  return X + BX * (Y + BY * Z);
+}
+
+namespace {
+
+inline int wrapi(int v, int n) { return ((v % n) + n) % n; }
+
+// Chebyshev distance from local cell c of a block to the nearest cell of the
+// neighbouring block in direction (dx, dy, dz)
+inline int cheb(int c, int dx, int dy, int dz) {
+  const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+  auto ax = [](int p, int d) { return d == 0 ? 0 : d < 0 ? p + 1 : 8 - p; };
+  return std::max(ax(x, dx), std::max(ax(y, dy), ax(z, dz)));
+}
+
+struct DomainLevel {
+  int nbx, nby, nbz;
+  bool px;
+  std::vector<uint8_t> region, refined;  // [nbz][nby][nbx]
+  // flat index of block (bx, by, bz) after periodic wrap, -1 outside x range
+  int64_t at(int bx, int by, int bz) const {
+    if (px) bx = wrapi(bx, nbx);
+    else if (bx < 0 || bx >= nbx) return -1;
+    by = wrapi(by, nby);
+    bz = wrapi(bz, nbz);
+    return bx + int64_t(nbx) * (by + int64_t(nby) * bz);
+  }
+  bool reg(int bx, int by, int bz) const {
+    const int64_t i = at(bx, by, bz);
+    return i >= 0 && region[i];
+  }
+  bool act(int bx, int by, int bz) const {
+    const int64_t i = at(bx, by, bz);
+    return i >= 0 && region[i] && !refined[i];
+  }
+};
+
+}  // namespace
+
+std::string build_plan(const lbm_grid& g, int model, int storage, double omega, GridPlan& P) {
+  char msg[256];
+  if (model != LBM_D3Q19_MRT_LES && model != LBM_D3Q27_FCLB) return "model must be 0 (D3Q19 MRT-LES) or 1 (D3Q27 FCLB)";
+  if (storage != LBM_F64 && storage != LBM_F32 && storage != LBM_F16) return "storage must be 0 (F64), 1 (F32) or 2 (F16)";
+  if (g.nbx < 1 || g.nby < 1 || g.nbz < 1) return "block counts must be >= 1";
+  if (g.levels < 1 || g.levels > kMaxL) return "levels must be in 1..4";
+  if (g.levels > 1 && g.refine == nullptr) return "refine flags required when levels > 1";
+  if (!(omega > 0.0 && omega < 2.0)) return "omega must be in (0, 2)";
+  const int L = g.levels;
+  const int64_t top = int64_t(g.nbx) * g.nby * g.nbz << (3 * (L - 1));
+  if (int64_t(g.nbx) << (L - 1) > (1 << 20) || int64_t(g.nby) << (L - 1) > (1 << 20) ||
+      int64_t(g.nbz) << (L - 1) > (1 << 20) || top > (int64_t(1) << 40))
+    return "grid too large";
+
+  P = GridPlan();
+  P.model = model;
+  P.storage = storage;
+  P.Q = model == LBM_D3Q19_MRT_LES ? 19 : 27;
+  P.levels = L;
+  P.periodic_x = g.periodic_x != 0;
+  const bool px = P.periodic_x;
+
+  // ---------------------------------------------------------------- levels
+  std::vector<DomainLevel> D(L);
+  int64_t off = 0;
+  for (int l = 0; l < L; ++l) {
+    DomainLevel& d = D[l];
+    d.nbx = g.nbx << l;
+    d.nby = g.nby << l;
+    d.nbz = g.nbz << l;
+    d.px = px;
+    const int64_t n = int64_t(d.nbx) * d.nby * d.nbz;
+    if (l == 0) d.region.assign(n, 1);
+    d.refined.assign(n, 0);
+    if (l < L - 1) {
+      int64_t cnt = 0;
+      for (int64_t i = 0; i < n; ++i) {
+        const uint8_t v = g.refine[off + i];
+        if (v > 1) return "refine flags must be 0 or 1";
+        if (v && !d.region[i]) {
+          snprintf(msg, sizeof msg, "refine flag on a block outside level %d", l);
+          return msg;
+        }
+        d.refined[i] = v;
+        cnt += v;
+      }
+      off += n;
+      if (cnt == 0) {
+        snprintf(msg, sizeof msg, "level %d refines no block", l);
+        return msg;
+      }
+      if (l >= 1) {  // nesting rule
+        for (int bz = 0; bz < d.nbz; ++bz)
+          for (int by = 0; by < d.nby; ++by)
+            for (int bx = 0; bx < d.nbx; ++bx) {
+              if (!d.refined[d.at(bx, by, bz)]) continue;
+              for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                  for (int dx = -1; dx <= 1; ++dx) {
+                    const int64_t j = d.at(bx + dx, by + dy, bz + dz);
+                    if (j >= 0 && !d.region[j]) {
+                      snprintf(msg, sizeof msg,
+                               "refined block (%d,%d,%d) of level %d touches the level boundary", bx,
+                               by, bz, l);
+                      return msg;
+                    }
+                  }
+            }
+      }
+      // children form the next level
+      DomainLevel& c = D[l + 1];
+      c.nbx = 2 * d.nbx;
+      c.nby = 2 * d.nby;
+      c.nbz = 2 * d.nbz;
+      c.region.assign(int64_t(c.nbx) * c.nby * c.nbz, 0);
+      for (int bz = 0; bz < d.nbz; ++bz)
+        for (int by = 0; by < d.nby; ++by)
+          for (int bx = 0; bx < d.nbx; ++bx)
+            if (d.refined[bx + int64_t(d.nbx) * (by + int64_t(d.nby) * bz)])
+              for (int k = 0; k < 8; ++k)
+                c.region[(2 * bx + (k & 1)) + int64_t(c.nbx) * ((2 * by + ((k >> 1) & 1)) +
+                                                               int64_t(c.nby) * (2 * bz + (k >> 2)))] = 1;
+    }
+  }
+
+  // ---------------------------------------------------------------- boxes and kinds
+  P.lv.resize(L);
+  const double tau00 = 1.0 / omega;
+  for (int l = 0; l < L; ++l) {
+    DomainLevel& d = D[l];
+    LevelPlan& lp = P.lv[l];
+    lp.l = l;
+    lp.nbx = d.nbx;
+    lp.nby = d.nby;
+    lp.nbz = d.nbz;
+    lp.NX = 8 * d.nbx;
+    lp.NY = 8 * d.nby;
+    lp.NZ = 8 * d.nbz;
+    lp.tau0 = 0.5 + std::ldexp(tau00 - 0.5, l);
+    const int64_t n = int64_t(d.nbx) * d.nby * d.nbz;
+    // used blocks: region, ghost (l >= 1, in domain, next to region), bc columns
+    std::vector<uint8_t> ghost(n, 0);
+    std::vector<uint8_t> usedx(d.nbx + 2, 0), usedy(d.nby, 0), usedz(d.nbz, 0);
+    std::vector<uint8_t> bcl(int64_t(d.nby) * d.nbz, 0), bch(int64_t(d.nby) * d.nbz, 0);
+    for (int bz = 0; bz < d.nbz; ++bz)
+      for (int by = 0; by < d.nby; ++by)
+        for (int bx = 0; bx < d.nbx; ++bx) {
+          const int64_t i = d.at(bx, by, bz);
+          if (d.region[i]) {
+            lp.level_blocks++;
+            usedx[bx + 1] = usedy[by] = usedz[bz] = 1;
+            if (!px) {
+              for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy) {
+                  const int64_t f = wrapi(by + dy, d.nby) + int64_t(d.nby) * wrapi(bz + dz, d.nbz);
+                  if (bx == 0) bcl[f] = 1;
+                  if (bx == d.nbx - 1) bch[f] = 1;
+                }
+            }
+            continue;
+          }
+          if (l == 0) continue;
+          bool adj = false;
+          for (int dz = -1; dz <= 1 && !adj; ++dz)
+            for (int dy = -1; dy <= 1 && !adj; ++dy)
+              for (int dx = -1; dx <= 1 && !adj; ++dx) adj = d.reg(bx + dx, by + dy, bz + dz);
+          if (adj) {
+            ghost[i] = 1;
+            usedx[bx + 1] = usedy[by] = usedz[bz] = 1;
+          }
+        }
+    for (int64_t f = 0; f < int64_t(d.nby) * d.nbz; ++f) {
+      if (bcl[f]) usedx[0] = usedy[f % d.nby] = usedz[f / d.nby] = 1;
+      if (bch[f]) usedx[d.nbx + 1] = usedy[f % d.nby] = usedz[f / d.nby] = 1;
+    }
+    auto range = [](const std::vector<uint8_t>& u, int shift, int& o, int& B) {
+      int lo = -1, hi = -1;
+      for (int i = 0; i < int(u.size()); ++i)
+        if (u[i]) {
+          if (lo < 0) lo = i;
+          hi = i;
+        }
+      o = lo - shift;
+      B = hi - lo + 1;
+    };
+    if (px) {
+      lp.ox = 0;
+      lp.BX = d.nbx;
+      lp.wrap[0] = true;
+      std::vector<uint8_t> ux(usedx.begin() + 1, usedx.end() - 1);
+      range(ux, 0, lp.ox, lp.BX);
+      lp.wrap[0] = lp.BX == d.nbx;
+    } else {
+      range(usedx, 1, lp.ox, lp.BX);
+      lp.wrap[0] = false;
+    }
+    range(usedy, 0, lp.oy, lp.BY);
+    range(usedz, 0, lp.oz, lp.BZ);
+    lp.wrap[1] = lp.BY == d.nby;
+    lp.wrap[2] = lp.BZ == d.nbz;
+    const int64_t nb = lp.nblocks();
+    if (nb * 512 * P.Q >= (int64_t(1) << 46)) return "level box too large";
+    lp.kind.assign(nb * 512, K_NONE);
+
+    auto box_of = [&](int bx, int by, int bz) -> int32_t {  // domain coords (wrapped)
+      if (px) bx = wrapi(bx, d.nbx);
+      by = wrapi(by, d.nby);
+      bz = wrapi(bz, d.nbz);
+      return lp.box_id(bx, by, bz);
+    };
+
+    // region blocks: active / hidden / refined cells; work items
+    for (int bz = 0; bz < d.nbz; ++bz)
+      for (int by = 0; by < d.nby; ++by)
+        for (int bx = 0; bx < d.nbx; ++bx) {
+          const int64_t i = d.at(bx, by, bz);
+          if (!d.region[i]) continue;
+          const int32_t b = lp.box_id(bx, by, bz);
+          if (b < 0) return "internal: region block outside its box";
+          // region blocks must not sit on a non-wrapping box face
+          const int X = bx - lp.ox, Y = by - lp.oy, Z = bz - lp.oz;
+          if ((!lp.wrap[0] && (X == 0 || X == lp.BX - 1)) || (!lp.wrap[1] && (Y == 0 || Y == lp.BY - 1)) ||
+              (!lp.wrap[2] && (Z == 0 || Z == lp.BZ - 1)))
+            return "internal: level block on the face of a non-periodic box";
+          uint8_t* k = &lp.kind[int64_t(b) * 512];
+          WorkItem w;
+          w.block = b;
+          w.level = uint8_t(l);
+          w.edges = uint8_t((lp.wrap[0] && X == 0 ? 1 : 0) | (lp.wrap[0] && X == lp.BX - 1 ? 2 : 0) |
+                            (lp.wrap[1] && Y == 0 ? 4 : 0) | (lp.wrap[1] && Y == lp.BY - 1 ? 8 : 0) |
+                            (lp.wrap[2] && Z == 0 ? 16 : 0) | (lp.wrap[2] && Z == lp.BZ - 1 ? 32 : 0));
+          if (!d.refined[i]) {
+            std::fill(k, k + 512, uint8_t(K_ACTIVE));
+            lp.active_cells += 512;
+            lp.updated_cells += 512;
+            w.mask = -1;
+            lp.items.push_back(w);
+            continue;
+          }
+          uint32_t m[16] = {0};
+          bool any = false;
+          for (int c = 0; c < 512; ++c) {
+            int dist = 99;
+            for (int dz = -1; dz <= 1; ++dz)
+              for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx)
+                  if ((dx | dy | dz) && d.act(bx + dx, by + dy, bz + dz))
+                    dist = std::min(dist, cheb(c, dx, dy, dz));
+            k[c] = dist == 1 ? K_HIDDEN1 : dist == 2 ? K_HIDDEN2 : K_REFINED;
+            if (dist == 1) {
+              m[c >> 5] |= 1u << (c & 31);
+              any = true;
+              lp.updated_cells++;
+            }
+            if (dist <= 2) lp.hidden_cells++;
+          }
+          if (any) {
+            w.mask = int16_t(lp.masks.size() / 16);
+            if (lp.masks.size() / 16 >= 32767) return "too many masked blocks";
+            lp.masks.insert(lp.masks.end(), m, m + 16);
+            lp.items.push_back(w);
+          }
+        }
+    // ghost blocks (l >= 1)
+    for (int bz = 0; bz < d.nbz; ++bz)
+      for (int by = 0; by < d.nby; ++by)
+        for (int bx = 0; bx < d.nbx; ++bx) {
+          const int64_t i = d.at(bx, by, bz);
+          if (!ghost[i]) continue;
+          const int32_t b = lp.box_id(bx, by, bz);
+          uint8_t* k = &lp.kind[int64_t(b) * 512];
+          for (int c = 0; c < 512; ++c) {
+            int dist = 99;
+            for (int dz = -1; dz <= 1; ++dz)
+              for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx)
+                  if ((dx | dy | dz) && d.reg(bx + dx, by + dy, bz + dz))
+                    dist = std::min(dist, cheb(c, dx, dy, dz));
+            if (dist == 1) {
+              k[c] = K_GHOST;
+              lp.ghost_cells++;
+            }
+          }
+        }
+    // boundary ghost columns
+    if (!px) {
+      for (int side = 0; side < 2; ++side) {
+        const std::vector<uint8_t>& col = side == 0 ? bcl : bch;
+        const int gbx = side == 0 ? -1 : d.nbx;
+        const int sbx = side == 0 ? 0 : d.nbx - 1;
+        const int gx = side == 0 ? 7 : 0, sx = side == 0 ? 0 : 7;
+        for (int bz = 0; bz < d.nbz; ++bz)
+          for (int by = 0; by < d.nby; ++by) {
+            if (!col[by + int64_t(d.nby) * bz]) continue;
+            const int32_t gb = lp.box_id(gbx, by, bz);
+            const int32_t sb = lp.box_id(sbx, by, bz);
+            if (gb < 0) return "internal: boundary block outside its box";
+            if (sb < 0) continue;
+            for (int cz = 0; cz < 8; ++cz)
+              for (int cy = 0; cy < 8; ++cy) {
+                const int sc = sx + 8 * cy + 64 * cz;
+                const uint8_t sk = lp.kind[int64_t(sb) * 512 + sc];
+                if (sk == K_NONE) continue;
+                const int gc = gx + 8 * cy + 64 * cz;
+                lp.kind[int64_t(gb) * 512 + gc] = K_BC;
+                lp.bc_cells++;
+                BCItem it{};
+                it.gblock = gb;
+                it.gcell = int16_t(gc);
+                it.type = int8_t(side);
+                it.sblock = sb;
+                it.scell = int16_t(sc);
+                it.y = 8 * by + cy;
+                it.z = 8 * bz + cz;
+                lp.bc.push_back(it);
+              }
+          }
+      }
+    }
+    (void)box_of;
+  }
+
+  // ---------------------------------------------------------------- interface lists
+  for (int l = 1; l < L; ++l) {
+    LevelPlan& f = P.lv[l];
+    const LevelPlan& c = P.lv[l - 1];
+    const DomainLevel& dc = D[l - 1];
+    for (int bz = f.oz; bz < f.oz + f.BZ; ++bz)
+      for (int by = f.oy; by < f.oy + f.BY; ++by)
+        for (int bx = f.ox; bx < f.ox + f.BX; ++bx) {
+          const int32_t b = f.box_id(bx, by, bz);
+          for (int cc = 0; cc < 512; ++cc) {
+            if (f.kind[int64_t(b) * 512 + cc] != K_GHOST) continue;
+            const int X = 8 * bx + (cc & 7), Y = 8 * by + ((cc >> 3) & 7), Z = 8 * bz + (cc >> 6);
+            int lo[3], hi[3];
+            uint8_t tb = 0;
+            const int XYZ[3] = {X, Y, Z};
+            const int NC[3] = {c.NX, c.NY, c.NZ};
+            for (int a = 0; a < 3; ++a) {
+              const int v = XYZ[a];
+              int i0 = (v - 1) >= 0 ? (v - 1) / 2 : -1;  // floor((v-1)/2) for v >= 0
+              int i1 = i0 + 1;
+              if (v % 2 == 0) tb |= uint8_t(1u << a);
+              if (a == 0 && !px) {
+                i0 = std::min(std::max(i0, 0), NC[a] - 1);
+                i1 = std::min(std::max(i1, 0), NC[a] - 1);
+              } else {
+                i0 = wrapi(i0, NC[a]);
+                i1 = wrapi(i1, NC[a]);
+              }
+              lo[a] = i0;
+              hi[a] = i1;
+            }
+            C2FItem it{};
+            it.fblock = b;
+            it.fcell = int16_t(cc);
+            it.tbits = tb;
+            for (int k = 0; k < 8; ++k) {
+              const int ix = (k & 1) ? hi[0] : lo[0];
+              const int iy = (k & 2) ? hi[1] : lo[1];
+              const int iz = (k & 4) ? hi[2] : lo[2];
+              const int32_t cb = c.box_id(ix >> 3, iy >> 3, iz >> 3);
+              const int ccell = (ix & 7) + 8 * (iy & 7) + 64 * (iz & 7);
+              if (cb < 0) return "internal: interpolation stencil outside the coarse box";
+              const uint8_t ck = c.kind[int64_t(cb) * 512 + ccell];
+              if (ck != K_ACTIVE && ck != K_HIDDEN1)
+                return "interpolation stencil leaves the updated coarse cells (grid too tight)";
+              it.cblock[k] = cb;
+              it.ccell[k] = int16_t(ccell);
+            }
+            f.c2f.push_back(it);
+          }
+        }
+    (void)dc;
+  }
+  for (int l = 0; l + 1 < L; ++l) {
+    LevelPlan& c = P.lv[l];
+    const LevelPlan& f = P.lv[l + 1];
+    for (int bz = c.oz; bz < c.oz + c.BZ; ++bz)
+      for (int by = c.oy; by < c.oy + c.BY; ++by)
+        for (int bx = c.ox; bx < c.ox + c.BX; ++bx) {
+          const int32_t b = c.box_id(bx, by, bz);
+          for (int cc = 0; cc < 512; ++cc) {
+            const uint8_t k = c.kind[int64_t(b) * 512 + cc];
+            if (k != K_HIDDEN1 && k != K_HIDDEN2) continue;
+            const int X = 8 * bx + (cc & 7), Y = 8 * by + ((cc >> 3) & 7), Z = 8 * bz + (cc >> 6);
+            F2CItem it{};
+            it.cblock = b;
+            it.ccell = int16_t(cc);
+            for (int ch = 0; ch < 8; ++ch) {
+              const int x = 2 * X + (ch & 1), y = 2 * Y + ((ch >> 1) & 1), z = 2 * Z + (ch >> 2);
+              const int32_t fb = f.box_id(x >> 3, y >> 3, z >> 3);
+              const int fc = (x & 7) + 8 * (y & 7) + 64 * (z & 7);
+              if (fb < 0 || f.kind[int64_t(fb) * 512 + fc] != K_ACTIVE)
+                return "internal: restriction child is not an active fine cell";
+              it.fblock[ch] = fb;
+              it.fcell[ch] = int16_t(fc);
+            }
+            c.f2c.push_back(it);
+          }
+        }
+  }
+
+  // ---------------------------------------------------------------- memory estimate
+  const size_t sb = storage_bytes(storage);
+  const bool aux = model == LBM_D3Q19_MRT_LES && L > 1;
+  const size_t rb = storage == LBM_F64 ? 8 : 4;
+  int64_t bytes = 0;
+  for (const LevelPlan& lp : P.lv) {
+    bytes += 2 * lp.nblocks() * 512 * P.Q * int64_t(sb);
+    if (aux) bytes += 2 * lp.nblocks() * 512 * int64_t(rb);
+    bytes += lp.nblocks() * 512;  // kinds
+    bytes += int64_t(lp.items.size() * sizeof(WorkItem) + lp.masks.size() * 4 +
+                     lp.c2f.size() * sizeof(C2FItem) + lp.f2c.size() * sizeof(F2CItem) +
+                     lp.bc.size() * sizeof(BCItem));
+  }
+  P.device_bytes = bytes;
+  return "";
+}
+
+}  // namespace lbm

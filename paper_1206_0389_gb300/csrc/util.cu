@@ -1,0 +1,213 @@
+// Utility kernels: dense <-> block staging (state, equilibrium initialisation,
+// macroscopic fields, body force), sampled gathers and the float64
+// mass/momentum audit.
+#include <cmath>
+
+#include "collide.cuh"
+#include "kernels.cuh"
+
+namespace lbm {
+
+template <int Q>
+__device__ __forceinline__ double shift_of(int i) {
+  return Q == 27 ? weight_rt<27>(i) : 0.0;  // D3Q19 stores the incompressible f itself
+}
+
+// locate dense level cell (x, y, z) in the level box; -1 if outside
+__device__ __forceinline__ int64_t box_index(int x, int y, int z, int ox, int oy, int oz, int BX,
+                                             int BY, int BZ) {
+  const int bx = (x >> 3) - ox, by = (y >> 3) - oy, bz = (z >> 3) - oz;
+  if (bx < 0 || bx >= BX || by < 0 || by >= BY || bz < 0 || bz >= BZ) return -1;
+  return (int64_t(bx) + int64_t(BX) * (by + int64_t(BY) * bz)) * kCells + (x & 7) + 8 * (y & 7) +
+         64 * (z & 7);
+}
+
+template <class M, class S>
+__global__ void k_slab(const SlabArgs a) {
+  using T = typename Store<S>::T;
+  constexpr int Q = M::Q;
+  const int64_t n = int64_t(a.NX) * a.NY * a.nz;
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int x = int(t % a.NX), y = int((t / a.NX) % a.NY), z = a.z0 + int(t / (int64_t(a.NX) * a.NY));
+  const int64_t j = box_index(x, y, z, a.ox, a.oy, a.oz, a.BX, a.BY, a.BZ);
+  const int64_t blk = j >= 0 ? j / kCells : 0, cell = j >= 0 ? j % kCells : 0;
+  S* f = reinterpret_cast<S*>(a.f) + blk * Q * kCells + cell;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  switch (a.mode) {
+    case SLAB_SET_STATE: {
+      if (j < 0) return;
+      for (int i = 0; i < Q; ++i) {
+        const double v = a.in[int64_t(i) * n + t];
+        if (isnan(v)) continue;
+        store_rt<S, Q>(f + i * kCells, i, T(v - shift_of<Q>(i)));
+      }
+      return;
+    }
+    case SLAB_GET_STATE: {
+      for (int i = 0; i < Q; ++i)
+        a.out[int64_t(i) * n + t] = j < 0 ? nan : double(load_rt<S, Q>(f + i * kCells, i)) + shift_of<Q>(i);
+      return;
+    }
+    case SLAB_INIT_EQ: {
+      if (j < 0) return;
+      const T rl = T(a.in[t] - 1.0);  // delta rho for both shifted models
+      const T ux = T(a.in[n + t]), uy = T(a.in[2 * n + t]), uz = T(a.in[3 * n + t]);
+      T feq[Q];
+      M::feq(rl, ux, uy, uz, feq);
+      for (int i = 0; i < Q; ++i) store_rt<S, Q>(f + i * kCells, i, feq[i]);
+      return;
+    }
+    case SLAB_MACRO: {
+      const uint8_t k = j < 0 ? uint8_t(K_NONE) : a.kind[j];
+      if (k != K_ACTIVE && k != K_HIDDEN1 && k != K_HIDDEN2) {
+        for (int c = 0; c < 4; ++c) a.out[c * n + t] = nan;
+        return;
+      }
+      double g[Q];
+      for (int i = 0; i < Q; ++i) g[i] = double(load_rt<S, Q>(f + i * kCells, i));
+      double rl = 0, jx = 0, jy = 0, jz = 0;
+      static_for<Q>([&](auto i) {
+        rl += g[i];
+        jx += Lattice<Q>::ex(i) * g[i];
+        jy += Lattice<Q>::ey(i) * g[i];
+        jz += Lattice<Q>::ez(i) * g[i];
+      });
+      const double rho = 1.0 + rl;
+      double ux = jx, uy = jy, uz = jz;
+      if (Q == 27) {
+        if (a.force != nullptr) {
+          const int64_t nn = int64_t(a.BX) * a.BY * a.BZ * kCells;
+          jx += 0.5 * a.force[j];
+          jy += 0.5 * a.force[nn + j];
+          jz += 0.5 * a.force[2 * nn + j];
+        }
+        ux = jx / rho;
+        uy = jy / rho;
+        uz = jz / rho;
+      }
+      a.out[t] = rho;
+      a.out[n + t] = ux;
+      a.out[2 * n + t] = uy;
+      a.out[3 * n + t] = uz;
+      return;
+    }
+    case SLAB_SET_FORCE: {
+      if (j < 0) return;
+      const int64_t nn = int64_t(a.BX) * a.BY * a.BZ * kCells;
+      for (int c = 0; c < 3; ++c) a.force[c * nn + j] = a.in[c * n + t];
+      return;
+    }
+  }
+}
+
+template <class M, class S>
+__global__ void k_gather(const GatherArgs a) {
+  constexpr int Q = M::Q;
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= a.n) return;
+  const long long c = a.cells[t];
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  const long long ncell = (long long)a.NX * a.NY * a.NZ;
+  int64_t j = -1;
+  if (c >= 0 && c < ncell) {
+    const int x = int(c % a.NX), y = int((c / a.NX) % a.NY), z = int(c / ((long long)a.NX * a.NY));
+    j = box_index(x, y, z, a.ox, a.oy, a.oz, a.BX, a.BY, a.BZ);
+  }
+  const S* f = reinterpret_cast<const S*>(a.f) + (j >= 0 ? (j / kCells) * Q * kCells + j % kCells : 0);
+  for (int i = 0; i < Q; ++i)
+    a.out[t * Q + i] = j < 0 ? nan : double(load_rt<S, Q>(f + i * kCells, i)) + shift_of<Q>(i);
+}
+
+// Float64 sums over active cells: (delta rho, j_x, j_y, j_z) times vol.
+template <class M, class S>
+__global__ void k_reduce(const ReduceArgs a) {
+  constexpr int Q = M::Q;
+  double s[4] = {0, 0, 0, 0};
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < a.ncells;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    if (a.kind[t] != K_ACTIVE) continue;
+    const S* f = reinterpret_cast<const S*>(a.f) + (t / kCells) * Q * kCells + t % kCells;
+    static_for<Q>([&](auto i) {
+      const double g = double(Store<S>::template get<Q, i>(f + int(i) * kCells));
+      s[0] += g;
+      s[1] += Lattice<Q>::ex(i) * g;
+      s[2] += Lattice<Q>::ey(i) * g;
+      s[3] += Lattice<Q>::ez(i) * g;
+    });
+  }
+  __shared__ double sh[4][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    double v = s[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[c][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double v = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
+    a.partial[blockIdx.x * 4 + threadIdx.x] = v * a.vol;
+  }
+}
+
+__global__ void k_reduce_final(const double* partial, int n, double* out, int* nonfinite) {
+  if (threadIdx.x < 4) {
+    double v = 0;
+    for (int i = 0; i < n; ++i) v += partial[i * 4 + threadIdx.x];
+    out[threadIdx.x] = v;
+    if (!isfinite(v)) atomicExch(nonfinite, 1);
+  }
+}
+
+template <class M, class S>
+static cudaError_t slab_ms(const SlabArgs& a, cudaStream_t st) {
+  const int64_t n = int64_t(a.NX) * a.NY * a.nz;
+  if (n == 0) return cudaSuccess;
+  k_slab<M, S><<<unsigned((n + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+template <class M, class S>
+static cudaError_t gather_ms(const GatherArgs& a, cudaStream_t st) {
+  if (a.n == 0) return cudaSuccess;
+  k_gather<M, S><<<unsigned((a.n + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+template <class M, class S>
+static cudaError_t reduce_ms(const ReduceArgs& a, int ctas, cudaStream_t st) {
+  k_reduce<M, S><<<ctas, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+#define LBM_DISPATCH(FN, ...)                                       \
+  if (model == LBM_D3Q19_MRT_LES) {                                 \
+    if (storage == LBM_F64) return FN<MrtLes, double>(__VA_ARGS__); \
+    if (storage == LBM_F32) return FN<MrtLes, float>(__VA_ARGS__);  \
+    return FN<MrtLes, __half>(__VA_ARGS__);                         \
+  }                                                                 \
+  if (storage == LBM_F64) return FN<Fclb, double>(__VA_ARGS__);     \
+  if (storage == LBM_F32) return FN<Fclb, float>(__VA_ARGS__);      \
+  return FN<Fclb, __half>(__VA_ARGS__);
+
+cudaError_t launch_slab(int model, int storage, const SlabArgs& a, cudaStream_t st) { LBM_DISPATCH(slab_ms, a, st) }
+cudaError_t launch_gather(int model, int storage, const GatherArgs& a, cudaStream_t st) { LBM_DISPATCH(gather_ms, a, st) }
+cudaError_t launch_reduce(int model, int storage, const ReduceArgs& a, int ctas, cudaStream_t st) {
+  LBM_DISPATCH(reduce_ms, a, ctas, st)
+}
+__global__ void k_fill(double* p, long long n, double v) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) p[t] = v;
+}
+cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_fill<<<unsigned((n + 255) / 256), 256, 0, st>>>(p, n, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_final(const double* partial, int n, double* out, int* nonfinite, cudaStream_t st) {
+  k_reduce_final<<<1, 32, 0, st>>>(partial, n, out, nonfinite);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,243 @@
+"""ctypes binding of liblbm.so: the same entry points as include/lbm.h.
+
+Only argument marshalling happens here (numpy arrays <-> pointers, status
+codes -> LbmError); every step of the update runs in the CUDA library.
+"""
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_int64, c_size_t, c_uint8, c_uint64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA = 0, -1, -2, -3
+LBM_ERR_TIMEOUT, LBM_ERR_NONFINITE, LBM_ERR_STATE = -4, -5, -6
+LBM_D3Q19_MRT_LES, LBM_D3Q27_FCLB = 0, 1
+LBM_F64, LBM_F32, LBM_F16 = 0, 1, 2
+LBM_MAX_LEVELS = 4
+MODELS = {"d3q19": LBM_D3Q19_MRT_LES, "d3q27": LBM_D3Q27_FCLB}
+STORAGES = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16}
+EXPORTED = ["lbm_plan", "lbm_create", "lbm_create_error", "lbm_set_inflow", "lbm_init_equilibrium",
+            "lbm_set_force", "lbm_step", "lbm_sync", "lbm_macroscopic", "lbm_mass_momentum",
+            "lbm_get_state", "lbm_set_state", "lbm_get_cells", "lbm_get_step", "lbm_set_step",
+            "lbm_set_profiling", "lbm_get_profile", "lbm_get_tuning", "lbm_last_error", "lbm_destroy"]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("lbm status %d: %s" % (status, msg))
+        self.status = status
+
+
+class lbm_grid(ctypes.Structure):
+    _fields_ = [("nbx", c_int), ("nby", c_int), ("nbz", c_int), ("periodic_x", c_int),
+                ("levels", c_int), ("refine", POINTER(c_uint8))]
+
+
+class lbm_plan_info(ctypes.Structure):
+    _fields_ = [("levels", c_int)] + [
+        (n, c_int64 * LBM_MAX_LEVELS) for n in
+        ("blocks", "level_blocks", "active_cells", "updated_cells", "hidden_cells", "ghost_cells",
+         "bc_cells")] + [("updates_per_coarse_step", c_int64),
+                         ("active_updates_per_coarse_step", c_int64), ("device_bytes", c_int64)]
+
+
+_lib = None
+
+
+def load():
+    """Load liblbm.so (built by __graft_entry__.build()); raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("liblbm.so not built at %s: run __graft_entry__.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P, D = POINTER, POINTER(c_double)
+    sig = {
+        "lbm_plan": (c_int, [P(lbm_grid), c_int, c_int, P(lbm_plan_info)]),
+        "lbm_create": (c_int, [P(c_void_p), c_int, c_int, P(lbm_grid), c_double, c_double, c_void_p]),
+        "lbm_create_error": (c_char_p, []),
+        "lbm_set_inflow": (c_int, [c_void_p, c_double, c_double, c_double, c_double, c_double, c_uint64]),
+        "lbm_init_equilibrium": (c_int, [c_void_p, c_int, D, D]),
+        "lbm_set_force": (c_int, [c_void_p, D]),
+        "lbm_step": (c_int, [c_void_p, c_int]),
+        "lbm_sync": (c_int, [c_void_p]),
+        "lbm_macroscopic": (c_int, [c_void_p, c_int, D, D]),
+        "lbm_mass_momentum": (c_int, [c_void_p, D]),
+        "lbm_get_state": (c_int, [c_void_p, c_int, D, c_size_t]),
+        "lbm_set_state": (c_int, [c_void_p, c_int, D, c_size_t]),
+        "lbm_get_cells": (c_int, [c_void_p, c_int, c_size_t, P(c_int64), D]),
+        "lbm_get_step": (c_int, [c_void_p, P(c_int64)]),
+        "lbm_set_step": (c_int, [c_void_p, c_int64]),
+        "lbm_set_profiling": (c_int, [c_void_p, c_int]),
+        "lbm_get_profile": (c_int, [c_void_p, D, P(c_int64)]),
+        "lbm_get_tuning": (c_int, [c_void_p, P(c_int), P(c_int)]),
+        "lbm_last_error": (c_char_p, [c_void_p]),
+        "lbm_destroy": (None, [c_void_p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(POINTER(c_double)) if a is not None else None
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_grid(nb, periodic_x=True, refine=()):
+    """lbm_grid from coarse block counts nb = (nbx, nby, nbz) and refine flags
+    (list of arrays shaped (nbz*2^l, nby*2^l, nbx*2^l)).  Returns (grid, keepalive)."""
+    flags = [np.ascontiguousarray(np.asarray(r, dtype=np.uint8)).reshape(-1) for r in refine]
+    buf = np.concatenate(flags) if flags else np.zeros(1, dtype=np.uint8)
+    g = lbm_grid(int(nb[0]), int(nb[1]), int(nb[2]), 1 if periodic_x else 0, len(flags) + 1,
+                 buf.ctypes.data_as(POINTER(c_uint8)))
+    return g, buf
+
+
+def lbm_plan(nb, periodic_x=True, refine=(), model="d3q19", storage="f32"):
+    lib = load()
+    g, keep = make_grid(nb, periodic_x, refine)
+    info = lbm_plan_info()
+    st = lib.lbm_plan(ctypes.byref(g), MODELS[model], STORAGES[storage], ctypes.byref(info))
+    if st != LBM_OK:
+        raise LbmError(st, "invalid grid")
+    return info
+
+
+class Context:
+    """An lbm_ctx handle with the level sizes needed to shape arrays."""
+
+    def __init__(self, handle, model, nb, levels):
+        self.h = handle
+        self.model = model
+        self.Q = 19 if model == "d3q19" else 27
+        self.nb = tuple(nb)
+        self.levels = levels
+
+    def dims(self, level):
+        s = 8 << level
+        return (self.nb[0] * s, self.nb[1] * s, self.nb[2] * s)  # NX, NY, NZ
+
+    def ncells(self, level):
+        NX, NY, NZ = self.dims(level)
+        return NX * NY * NZ
+
+
+def _check(ctx, st):
+    if st != LBM_OK:
+        msg = load().lbm_last_error(ctx.h if ctx is not None else None)
+        raise LbmError(st, msg.decode() if msg else "")
+
+
+def lbm_create(model, storage, nb, periodic_x=True, refine=(), omega=1.0, cs=0.0, stream=None):
+    lib = load()
+    g, keep = make_grid(nb, periodic_x, refine)
+    h = c_void_p()
+    st = lib.lbm_create(ctypes.byref(h), MODELS[model], STORAGES[storage], ctypes.byref(g),
+                        float(omega), float(cs), stream)
+    if st != LBM_OK:
+        raise LbmError(st, lib.lbm_create_error().decode())
+    return Context(h, model, nb, g.levels)
+
+
+def lbm_destroy(ctx):
+    if ctx is not None and ctx.h:
+        load().lbm_destroy(ctx.h)
+        ctx.h = None
+
+
+def lbm_set_inflow(ctx, y0, z0, diameter, u_in, perturb=0.01, seed=0):
+    _check(ctx, load().lbm_set_inflow(ctx.h, y0, z0, diameter, u_in, perturb, int(seed)))
+
+
+def lbm_init_equilibrium(ctx, level, rho=None, u=None):
+    r, v = _f64(rho), _f64(u)
+    _check(ctx, load().lbm_init_equilibrium(ctx.h, level, _dptr(r), _dptr(v)))
+
+
+def lbm_set_force(ctx, F):
+    a = _f64(F)
+    _check(ctx, load().lbm_set_force(ctx.h, _dptr(a)))
+
+
+def lbm_step(ctx, n=1):
+    _check(ctx, load().lbm_step(ctx.h, int(n)))
+
+
+def lbm_sync(ctx):
+    _check(ctx, load().lbm_sync(ctx.h))
+
+
+def lbm_macroscopic(ctx, level):
+    NX, NY, NZ = ctx.dims(level)
+    rho = np.empty((NZ, NY, NX))
+    u = np.empty((3, NZ, NY, NX))
+    _check(ctx, load().lbm_macroscopic(ctx.h, level, _dptr(rho), _dptr(u)))
+    return rho, u
+
+
+def lbm_mass_momentum(ctx):
+    out = np.empty(4)
+    _check(ctx, load().lbm_mass_momentum(ctx.h, _dptr(out)))
+    return out
+
+
+def lbm_get_state(ctx, level):
+    NX, NY, NZ = ctx.dims(level)
+    f = np.empty((ctx.Q, NZ, NY, NX))
+    _check(ctx, load().lbm_get_state(ctx.h, level, _dptr(f), f.size))
+    return f
+
+
+def lbm_set_state(ctx, level, f):
+    a = _f64(f)
+    _check(ctx, load().lbm_set_state(ctx.h, level, _dptr(a), a.size))
+
+
+def lbm_get_cells(ctx, level, cells):
+    c = np.ascontiguousarray(cells, dtype=np.int64)
+    out = np.empty((c.size, ctx.Q))
+    _check(ctx, load().lbm_get_cells(ctx.h, level, c.size, c.ctypes.data_as(POINTER(c_int64)),
+                                     _dptr(out)))
+    return out
+
+
+def lbm_get_step(ctx):
+    s = c_int64()
+    _check(ctx, load().lbm_get_step(ctx.h, ctypes.byref(s)))
+    return s.value
+
+
+def lbm_set_step(ctx, step):
+    _check(ctx, load().lbm_set_step(ctx.h, int(step)))
+
+
+def lbm_set_profiling(ctx, enable):
+    _check(ctx, load().lbm_set_profiling(ctx.h, 1 if enable else 0))
+
+
+def lbm_get_profile(ctx):
+    ms = np.zeros(5)
+    n = (c_int64 * 5)()
+    _check(ctx, load().lbm_get_profile(ctx.h, _dptr(ms), n))
+    return ms, np.array(list(n), dtype=np.int64)
+
+
+def lbm_get_tuning(ctx):
+    t, c = c_int(), c_int()
+    _check(ctx, load().lbm_get_tuning(ctx.h, ctypes.byref(t), ctypes.byref(c)))
+    return t.value, c.value
+
+
+def lbm_last_error(ctx):
+    return load().lbm_last_error(ctx.h).decode()

@@ -1,0 +1,109 @@
+"""CPU tests of the C ABI: the library loads, exports every symbol declared in
+include/lbm.h, plans grids on the host exactly like the oracle's masks, and
+reports errors without touching a GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle.grid import build_levels
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+lbm = pytest.importorskip("paper_1206_0389_gb300.lbm")
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = lbm.load()
+    names = declared_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(lbm.EXPORTED)
+
+
+def slab_refine(nb, lo, hi):
+    r = np.zeros((nb[2], nb[1], nb[0]), dtype=bool)
+    r[:, :, lo:hi] = True
+    return r
+
+
+GRIDS = {
+    "slab2": ((4, 2, 2), True, [slab_refine((4, 2, 2), 1, 3)]),
+    "slab2_open": ((4, 2, 2), False, [slab_refine((4, 2, 2), 0, 2)]),
+    "three": ((3, 2, 2), True, None),
+    "jet_small": ((6, 4, 4), False, None),
+}
+
+
+def grid(name):
+    nb, px, ref = GRIDS[name]
+    if name == "three":
+        r0 = np.zeros((2, 2, 3), dtype=bool)
+        r0[:, :, 0:2] = True
+        r1 = np.zeros((4, 4, 6), dtype=bool)
+        r1[1:3, 1:3, 1:3] = True
+        ref = [r0, r1]
+    if name == "jet_small":
+        flags, _ = synth.jet_two_level(6, 4, 4, radius=12.0)
+        ref = flags
+    return nb, px, ref
+
+
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_plan_counts_match_oracle_masks(name):
+    nb, px, ref = grid(name)
+    info = lbm.lbm_plan(nb, px, ref, "d3q27", "f32")
+    lv = build_levels(nb, px, [torch.from_numpy(r) for r in ref])
+    assert info.levels == len(lv)
+    upd = 0
+    for l, L in enumerate(lv):
+        assert info.active_cells[l] == int(L.active.sum())
+        assert info.updated_cells[l] == int(L.update.sum())
+        assert info.hidden_cells[l] == int((L.hidden1 | L.hidden2).sum())
+        assert info.ghost_cells[l] == int(L.ghost.sum())
+        assert info.level_blocks[l] == int(L.region_blocks.sum())
+        upd += int(L.update.sum()) << l
+    assert info.updates_per_coarse_step == upd
+
+
+def test_jet_plan_sizes():
+    flags, _ = synth.jet_two_level()
+    info = lbm.lbm_plan((48, 24, 24), False, flags, "d3q27", "f32")
+    assert info.active_cells[0] == 13_369_344 and info.active_cells[1] == 6_291_456
+    assert info.active_updates_per_coarse_step == 25_952_256
+
+
+def test_plan_rejects_bad_grids():
+    r0 = np.zeros((2, 2, 3), dtype=bool)
+    r0[:, :, 0:2] = True
+    r1 = np.zeros((4, 4, 6), dtype=bool)
+    r1[1:3, 1:3, 2:4] = True   # x block 3 touches the level-1 boundary at x = 4
+    with pytest.raises(ValueError):
+        build_levels((3, 2, 2), True, [torch.from_numpy(r0), torch.from_numpy(r1)])
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_plan((3, 2, 2), True, [r0, r1])
+    bad = np.zeros((2, 2, 3), dtype=bool)
+    with pytest.raises(lbm.LbmError):           # a level that refines nothing
+        lbm.lbm_plan((3, 2, 2), True, [bad, np.zeros((4, 4, 6), dtype=bool)])
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_plan((0, 2, 2), True, [])
+
+
+def test_create_without_gpu_reports_cuda_error():
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create("d3q19", "f32", (2, 2, 2))
+    assert e.value.status == lbm.LBM_ERR_CUDA
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create("d3q19", "f32", (2, 2, 2), omega=2.5)
+    assert e.value.status == lbm.LBM_ERR_ARG
