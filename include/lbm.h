@@ -167,6 +167,30 @@ int lbm_get_profile(lbm_ctx* ctx, double ms[5], int64_t launches[5]);
  * threads per CTA and CTAs per launch (0 = one CTA per block). */
 int lbm_get_tuning(const lbm_ctx* ctx, int* threads, int* ctas_per_sm);
 
+/* Mass/momentum audit for callers that cannot let the library allocate
+ * device memory: code running under CUDA stream capture (allocation is not
+ * capturable), frameworks whose own caching pool owns all device memory, and
+ * time-critical loops that must not stall on an allocation.  The paper has no
+ * counterpart; it is a service entry point of this library.
+ *   f        device array of nblocks blocks in the library's storage layout,
+ *            [block][Q][512 cells] (cell x + 8y + 64z), shifted and typed as
+ *            described for lbm_storage; every cell is summed with volume 1.
+ *   out      device array of 4 doubles the caller owns; receives
+ *            {sum (rho - 1), sum j_x, sum j_y, sum j_z} in float64.
+ *   cuda_stream  cudaStream_t the work is enqueued on (NULL = legacy stream);
+ *            the call does not synchronise.
+ * No cudaMalloc/cudaFree: partial sums go to a static device array of
+ * LBM_NOALLOC_MAX_BLOCKS * 4 doubles (2 MiB) that every GPU loading the
+ * library keeps until exit.  Returns LBM_ERR_ARG for a bad model/storage, a
+ * NULL pointer, or nblocks outside 1..LBM_NOALLOC_MAX_BLOCKS (the static
+ * array holds one partial sum per block); LBM_ERR_CUDA on a launch error.
+ * All calls share the array: calls that overlap on the same GPU race.  The
+ * first call on a device looks up the array's address; make it before any
+ * stream capture. */
+#define LBM_NOALLOC_MAX_BLOCKS 65536
+int lbm_mass_momentum_noalloc(int model, int storage, const void* f, int64_t nblocks, double* out,
+                              void* cuda_stream);
+
 /* Message describing the last failure on ctx ("" if none). */
 const char* lbm_last_error(const lbm_ctx* ctx);
 

@@ -22,7 +22,9 @@ STORAGES = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16}
 EXPORTED = ["lbm_plan", "lbm_create", "lbm_create_error", "lbm_set_inflow", "lbm_init_equilibrium",
             "lbm_set_force", "lbm_step", "lbm_sync", "lbm_macroscopic", "lbm_mass_momentum",
             "lbm_get_state", "lbm_set_state", "lbm_get_cells", "lbm_get_step", "lbm_set_step",
-            "lbm_set_profiling", "lbm_get_profile", "lbm_get_tuning", "lbm_last_error", "lbm_destroy"]
+            "lbm_set_profiling", "lbm_get_profile", "lbm_get_tuning", "lbm_last_error", "lbm_destroy",
+            "lbm_mass_momentum_noalloc"]
+NOALLOC_MAX_BLOCKS = 65536
 
 
 class LbmError(RuntimeError):
@@ -77,6 +79,7 @@ def load():
         "lbm_get_tuning": (c_int, [c_void_p, P(c_int), P(c_int)]),
         "lbm_last_error": (c_char_p, [c_void_p]),
         "lbm_destroy": (None, [c_void_p]),
+        "lbm_mass_momentum_noalloc": (c_int, [c_int, c_int, c_void_p, c_int64, c_void_p, c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -241,3 +244,18 @@ def lbm_get_tuning(ctx):
 
 def lbm_last_error(ctx):
     return load().lbm_last_error(ctx.h).decode()
+
+
+def lbm_mass_momentum_noalloc(model, storage, f_ptr, nblocks, out_ptr, stream=None):
+    """Float64 mass/momentum sums of a caller-owned device array (library
+    storage layout) into a caller-owned device array of 4 doubles, without
+    any device allocation (see include/lbm.h).  Pointers are integers (e.g.
+    torch.Tensor.data_ptr()); the call is asynchronous on `stream`."""
+    if not 1 <= int(nblocks) <= NOALLOC_MAX_BLOCKS:
+        raise LbmError(LBM_ERR_ARG, "nblocks=%d outside 1..%d: the static scratch holds one "
+                       "partial sum per block" % (int(nblocks), NOALLOC_MAX_BLOCKS))
+    st = load().lbm_mass_momentum_noalloc(MODELS[model], STORAGES[storage], c_void_p(int(f_ptr)),
+                                          int(nblocks), c_void_p(int(out_ptr)),
+                                          None if stream is None else c_void_p(int(stream)))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_mass_momentum_noalloc failed")
