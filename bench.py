@@ -43,7 +43,7 @@ BYTES_PER_UPDATE = {("d3q27", "f32"): 216, ("d3q27", "f16"): 108, ("d3q27", "f64
                     ("d3q19", "f32"): 152, ("d3q19", "f16"): 76, ("d3q19", "f64"): 304}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "update_kernel_traffic.txt")
 KERNEL_SOURCES = ["paper_1206_0389_gb300/csrc/update.cu", "paper_1206_0389_gb300/csrc/collide.cuh",
-                  "paper_1206_0389_gb300/csrc/lattice.cuh", "paper_1206_0389_gb300/csrc/kernels.cuh"]
+                  "paper_1206_0389_gb300/csrc/lattice.cuh"]
 
 
 # ----------------------------------------------------------------- distributed helpers
@@ -286,6 +286,14 @@ def ours(args):
     field = synth.spectrum_field(N_GRID, seed=1206 + rank)
     K, W = args.steps, args.warmup
 
+    if args.kernel_only:
+        r = run_uniform(lbm, torch, "d3q27", "f32", field, K, W, stream)
+        lbm.lbm_destroy(r["ctx"])
+        if rank == 0:
+            print(json.dumps({"kernel_only": True, "ms_per_step": r["ms"] / K,
+                              "kernel_ms": r["kernel_ms"], "tuning": r["tuning"]}), flush=True)
+        return
+
     # headline: D3Q27 FCLB FP32
     barrier(dist)
     torch.cuda.synchronize()
@@ -423,6 +431,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="headline only (no variants)")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="only the headline stream-collide steps (for ncu captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
