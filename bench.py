@@ -250,6 +250,49 @@ def run_jet(lbm, torch, model, steps, warmup, stream):
             "launches_per_coarse_step": int(pn.sum()) // 3}
 
 
+def run_adjoint(lbm, torch, stream, T=256, every=16, N=96):
+    """Adjoint of the forced FCLB update (96^3, FP32, T = 256, checkpoints
+    every 16): device time of the T forward steps vs the checkpointed forward
+    and the recompute + adjoint backward sweep."""
+    import synth
+    omega = 1.0 / (3 * 0.005 + 0.5)
+    rho, u = synth.spectrum_field(N, seed=4096)
+    F = synth.random_force((N, N, N), 4096, sigma=1e-6)
+    ctx = lbm.lbm_create("d3q27", "f32", (N // 8,) * 3, True, [], omega, 0.0, stream.cuda_stream)
+    lbm.lbm_init_equilibrium(ctx, 0, rho, u)
+    lbm.lbm_set_force(ctx, F)
+    f0 = lbm.lbm_get_state(ctx, 0)
+    lbm.lbm_step(ctx, 3)
+    lbm.lbm_sync(ctx)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lbm.lbm_step(ctx, T)
+    e1.record(stream)
+    e1.synchronize()
+    fwd_ms = e0.elapsed_time(e1)
+    lbm.lbm_set_state(ctx, 0, f0)
+    e0.record(stream)
+    lbm.lbm_adjoint_forward(ctx, T, every)
+    e1.record(stream)
+    e1.synchronize()
+    ckfwd_ms = e0.elapsed_time(e1)
+    lam = np.zeros((27, N, N, N))
+    c = N // 2
+    lam[:, c - 8:c + 8, c - 8:c + 8, c - 8:c + 8] = 1e-3
+    lbm.lbm_set_profiling(ctx, True)
+    lbm.lbm_adjoint_backward(ctx, lam)
+    pms, _ = lbm.lbm_get_profile(ctx)
+    lbm.lbm_set_profiling(ctx, False)
+    lbm.lbm_destroy(ctx)
+    sweep_ms = float(pms[4])
+    return {"grid": "%d^3" % N, "T": T, "checkpoint_every": every,
+            "forward_ms": round(fwd_ms, 3), "checkpointed_forward_ms": round(ckfwd_ms, 3),
+            "backward_sweep_ms": round(sweep_ms, 3),
+            "backward_over_forward": round(sweep_ms / fwd_ms, 3),
+            "adjoint_total_over_forward": round((ckfwd_ms + sweep_ms) / fwd_ms, 3)}
+
+
 def cpu_baseline(seconds=12.0):
     """The FP64 oracle as it stands on the host cores: D3Q27 FCLB on a 16^3
     periodic sample of the decaying-turbulence workload."""
@@ -367,6 +410,7 @@ def ours(args):
             lbm.lbm_destroy(r["ctx"])
         for model in ("d3q27", "d3q19"):
             variants["jet_2level_%s_f32" % model] = run_jet(lbm, torch, model, max(10, K // 4), 3, stream)
+        variants["adjoint_d3q27_f32"] = run_adjoint(lbm, torch, stream)
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": K,

@@ -156,10 +156,28 @@ int lbm_get_cells(lbm_ctx* ctx, int level, size_t n, const int64_t* cells, doubl
 int lbm_get_step(const lbm_ctx* ctx, int64_t* step);
 int lbm_set_step(lbm_ctx* ctx, int64_t step);
 
+/* Discrete adjoint of the forced D3Q27 FCLB update (single periodic level,
+ * F32 or F64 storage; the paper has no adjoint: this serves gradient-based
+ * studies of the same update).  Two phases with sqrt(T)-style checkpointing:
+ * lbm_adjoint_forward advances T steps from the current state (with the force
+ * of lbm_set_force), keeping a copy of the state every checkpoint_every steps;
+ * the final state is then the context's state.  lbm_adjoint_backward takes
+ * dL/df_T (host, float64, dense [27][NZ][NY][NX], w.r.t. the distributions
+ * after step T) and returns dL/dF (host, float64, dense [3][NZ][NY][NX]) of a
+ * force held constant over the T steps.  Each segment of checkpoint_every
+ * steps is recomputed from its checkpoint, then swept backwards with the
+ * adjoint stream-collide kernel.  Device memory: (T/checkpoint_every +
+ * checkpoint_every + 2) states plus the dL/dF accumulator.  LBM_ERR_STATE for
+ * other grids or models, or backward without a forward. */
+int lbm_adjoint_forward(lbm_ctx* ctx, int T, int checkpoint_every);
+int lbm_adjoint_backward(lbm_ctx* ctx, const double* dLdf_T, double* dLdF);
+
 /* Kernel timing: when enabled, lbm_step launches kernels directly (no graph)
  * between CUDA events on the context stream and accumulates per-kind device
  * time.  kinds: 0 update (stream-collide), 1 coarse-to-fine, 2 fine-to-coarse,
- * 3 boundary, 4 other.  ms[k] total milliseconds, launches[k] launch counts. */
+ * 3 boundary, 4 other (an lbm_adjoint_backward call adds the device time of
+ * its recompute + adjoint sweep here as one entry).  ms[k] total
+ * milliseconds, launches[k] launch counts. */
 int lbm_set_profiling(lbm_ctx* ctx, int enable);
 int lbm_get_profile(lbm_ctx* ctx, double ms[5], int64_t launches[5]);
 

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "liblbm.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["update.cu", "interface.cu", "util.cu", "api.cu", "plan.cpp", "noalloc.cu"]
+SOURCES = ["update.cu", "interface.cu", "util.cu", "api.cu", "plan.cpp", "noalloc.cu", "adjoint.cu"]
 
 
 def nvcc():

@@ -81,6 +81,13 @@ struct lbm_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graphs_valid = false;
   bool profiling = false;
+  // adjoint: checkpoints every `every` steps, segment buffers, lambda, dL/dF
+  int adj_T = 0, adj_every = 0;
+  bool adj_ready = false;
+  std::vector<void*> adj_ck, adj_seg;
+  void* adj_lam[2] = {nullptr, nullptr};
+  void* adj_gF = nullptr;
+  size_t adj_state_bytes = 0;
   double prof_ms[5] = {0, 0, 0, 0, 0};
   int64_t prof_n[5] = {0, 0, 0, 0, 0};
   std::string err;
@@ -133,6 +140,11 @@ void free_all(lbm_ctx* c) {
   cudaFree(c->d_out);
   cudaFree(c->d_flag);
   cudaFree(c->stage);
+  for (void* p : c->adj_ck) cudaFree(p);
+  for (void* p : c->adj_seg) cudaFree(p);
+  cudaFree(c->adj_lam[0]);
+  cudaFree(c->adj_lam[1]);
+  cudaFree(c->adj_gF);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -380,7 +392,7 @@ int cur_parity(const lbm_ctx* ctx, int level) { return level == 0 ? ctx->parity0
 // hout[c] are the host arrays of the comps components ([NZ][NY][NX] each);
 // a NULL input component is filled with fill[c] on the device.
 int slab_transfer(lbm_ctx* ctx, int level, int mode, const double* const* hin, double* const* hout,
-                  int comps, const double* fill = nullptr) {
+                  int comps, const double* fill = nullptr, void* raw = nullptr) {
   const LevelPlan& lp = ctx->plan.lv[level];
   const int64_t plane = int64_t(lp.NX) * lp.NY;
   int nz = 8;
@@ -417,6 +429,7 @@ int slab_transfer(lbm_ctx* ctx, int level, int mode, const double* const* hin, d
     a.in = ctx->stage;
     a.out = ctx->stage;
     a.mode = mode;
+    a.raw = raw;
     CK(launch_slab(ctx->model, ctx->storage, a, ctx->stream));
     if (hout)
       for (int c = 0; c < comps; ++c)
@@ -829,6 +842,132 @@ int lbm_get_profile(lbm_ctx* ctx, double ms[5], int64_t launches[5]) {
     launches[k] = ctx->prof_n[k];
   }
   return LBM_OK;
+}
+
+int lbm_adjoint_forward(lbm_ctx* ctx, int T, int checkpoint_every) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (ctx->model != LBM_D3Q27_FCLB || ctx->L != 1 || !ctx->plan.periodic_x)
+    return fail(ctx, LBM_ERR_STATE, "the adjoint is defined for single-level periodic D3Q27 grids");
+  if (ctx->storage == LBM_F16) return fail(ctx, LBM_ERR_STATE, "the adjoint needs F32 or F64 storage");
+  if (T < 1 || checkpoint_every < 1 || checkpoint_every > T)
+    return fail(ctx, LBM_ERR_ARG, "need T >= 1 and 1 <= checkpoint_every <= T");
+  const LevelPlan& lp = ctx->plan.lv[0];
+  const size_t sb = size_t(lp.nblocks()) * 512 * 27 * storage_bytes(ctx->storage);
+  const int nck = (T + checkpoint_every - 1) / checkpoint_every;
+  if (ctx->adj_state_bytes != sb || int(ctx->adj_ck.size()) < nck || int(ctx->adj_seg.size()) < checkpoint_every) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (void* p : ctx->adj_ck) cudaFree(p);
+    for (void* p : ctx->adj_seg) cudaFree(p);
+    cudaFree(ctx->adj_lam[0]);
+    cudaFree(ctx->adj_lam[1]);
+    cudaFree(ctx->adj_gF);
+    ctx->adj_ck.clear();
+    ctx->adj_seg.clear();
+    ctx->adj_lam[0] = ctx->adj_lam[1] = ctx->adj_gF = nullptr;
+    ctx->adj_state_bytes = sb;
+    auto grab = [&](void** p, size_t n) -> int {
+      cudaError_t e = cudaMalloc(p, n);
+      if (e != cudaSuccess) return fail(ctx, LBM_ERR_OOM, std::string("adjoint buffers: ") + cudaGetErrorString(e));
+      return LBM_OK;
+    };
+    ctx->adj_ck.assign(nck, nullptr);
+    ctx->adj_seg.assign(checkpoint_every, nullptr);
+    for (auto& p : ctx->adj_ck)
+      if (int rc = grab(&p, sb)) return rc;
+    for (size_t k = 1; k < ctx->adj_seg.size(); ++k)
+      if (int rc = grab(&ctx->adj_seg[k], sb)) return rc;
+    for (int k = 0; k < 2; ++k)
+      if (int rc = grab(&ctx->adj_lam[k], sb)) return rc;
+    if (int rc = grab(&ctx->adj_gF, size_t(lp.nblocks()) * 512 * 3 * real_bytes(ctx->storage))) return rc;
+  }
+  if (ctx->need_restrict) {
+    int rc = restrict_all(ctx);
+    if (rc) return rc;
+  }
+  if (!ctx->graphs_valid) {
+    int rc = build_graphs(ctx);
+    if (rc) return rc;
+  }
+  ctx->adj_ready = false;
+  for (int t = 0; t < T; ++t) {
+    if (t % checkpoint_every == 0)
+      CK(cudaMemcpyAsync(ctx->adj_ck[t / checkpoint_every], ctx->dl[0].f[ctx->parity0], sb,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaGraphLaunch(ctx->graph[ctx->parity0], ctx->stream));
+    ctx->parity0 ^= 1;
+    ctx->step++;
+  }
+  ctx->adj_T = T;
+  ctx->adj_every = checkpoint_every;
+  ctx->adj_ready = true;
+  return LBM_OK;
+}
+
+int lbm_adjoint_backward(lbm_ctx* ctx, const double* dLdf_T, double* dLdF) {
+  if (!ctx || !dLdf_T || !dLdF) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+  if (!ctx->adj_ready) return fail(ctx, LBM_ERR_STATE, "call lbm_adjoint_forward first");
+  const LevelPlan& lp = ctx->plan.lv[0];
+  const size_t n = size_t(lp.NX) * lp.NY * lp.NZ;
+  if (!all_finite(dLdf_T, 27 * n)) return fail(ctx, LBM_ERR_NONFINITE, "non-finite dL/df_T");
+  const size_t rb = real_bytes(ctx->storage);
+  // lambda_T into the block layout
+  CK(cudaMemsetAsync(ctx->adj_lam[0], 0, ctx->adj_state_bytes, ctx->stream));
+  std::vector<const double*> hin(27);
+  for (int i = 0; i < 27; ++i) hin[i] = dLdf_T + i * n;
+  int rc = slab_transfer(ctx, 0, SLAB_SET_LAMBDA, hin.data(), nullptr, 27, nullptr, ctx->adj_lam[0]);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(ctx->adj_gF, 0, size_t(lp.nblocks()) * 512 * 3 * rb, ctx->stream));
+  // the update launch of the single level, retargeted to segment buffers
+  std::vector<Op> ops = build_schedule(ctx, 0);
+  UpdateArgs ua{};
+  for (const Op& op : ops)
+    if (op.kind == Op::UPDATE) ua = op.ua;
+  AdjointArgs aa{};
+  aa.dLdF = ctx->adj_gF;
+  aa.force = ctx->has_force ? ctx->dl[0].force : nullptr;
+  aa.BX = lp.BX;
+  aa.BY = lp.BY;
+  aa.BZ = lp.BZ;
+  aa.nblocks = int(lp.nblocks());
+  aa.omega = 1.0 / lp.tau0;
+  const int T = ctx->adj_T, every = ctx->adj_every;
+  const int nck = (T + every - 1) / every;
+  int cur = 0;
+  cudaEvent_t pe0 = nullptr, pe1 = nullptr;
+  if (ctx->profiling) {
+    CK(cudaEventCreate(&pe0));
+    CK(cudaEventCreate(&pe1));
+    CK(cudaEventRecord(pe0, ctx->stream));
+  }
+  for (int s = nck - 1; s >= 0; --s) {
+    const int t0 = s * every, t1 = std::min(T, t0 + every), m = t1 - t0;
+    // segment slot 0 is the checkpoint itself; slots 1.. hold the recomputed states
+    auto seg = [&](int k) { return k == 0 ? ctx->adj_ck[s] : ctx->adj_seg[k]; };
+    for (int k = 0; k + 1 < m; ++k) {
+      ua.lv[0].src = seg(k);
+      ua.lv[0].dst = seg(k + 1);
+      CK(launch_update(ctx->model, ctx->storage, ua, ctx->threads, ctx->ctas, ctx->stream));
+    }
+    for (int k = m - 1; k >= 0; --k) {
+      aa.f_t = seg(k);
+      aa.lam_in = ctx->adj_lam[cur];
+      aa.lam_out = ctx->adj_lam[1 - cur];
+      CK(launch_adjoint(ctx->storage, aa, ctx->stream));
+      cur ^= 1;
+    }
+  }
+  if (ctx->profiling) {
+    CK(cudaEventRecord(pe1, ctx->stream));
+    CK(cudaEventSynchronize(pe1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, pe0, pe1));
+    ctx->prof_ms[4] += ms;
+    ctx->prof_n[4] += 1;
+    cudaEventDestroy(pe0);
+    cudaEventDestroy(pe1);
+  }
+  double* hout[3] = {dLdF, dLdF + n, dLdF + 2 * n};
+  return slab_transfer(ctx, 0, SLAB_GET_FIELD3, nullptr, hout, 3, nullptr, ctx->adj_gF);
 }
 
 int lbm_get_tuning(const lbm_ctx* ctx, int* threads, int* ctas) {

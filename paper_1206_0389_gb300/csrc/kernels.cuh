@@ -126,7 +126,7 @@ cudaError_t launch_step_inc(long long* step, cudaStream_t st);
 
 // dense <-> block staging for one slab of cell layers [z0, z0 + nz) of a level
 enum SlabMode { SLAB_SET_STATE = 0, SLAB_GET_STATE = 1, SLAB_INIT_EQ = 2, SLAB_MACRO = 3,
-                SLAB_SET_FORCE = 4 };
+                SLAB_SET_FORCE = 4, SLAB_SET_LAMBDA = 5, SLAB_GET_FIELD3 = 6 };
 struct SlabArgs {
   void* f;                // level storage (current buffer)
   const uint8_t* kind;    // [nblocks][512] cell kinds
@@ -136,6 +136,7 @@ struct SlabArgs {
   const double* in;       // SET_STATE: f [Q][n]; INIT_EQ: rho [n], u [3][n]; SET_FORCE: F [3][n]
   double* out;            // GET_STATE: f [Q][n]; MACRO: rho [n], u [3][n]
   int mode;
+  void* raw;              // SET_LAMBDA: [block][Q][512] (compute type); GET_FIELD3: [3][nblocks*512]
 };
 cudaError_t launch_slab(int model, int storage, const SlabArgs& a, cudaStream_t st);
 cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t st);
@@ -149,6 +150,18 @@ struct GatherArgs {
   double* out;  // [n][Q]
 };
 cudaError_t launch_gather(int model, int storage, const GatherArgs& a, cudaStream_t st);
+
+// one adjoint step of a periodic single-level D3Q27 grid (adjoint.cu)
+struct AdjointArgs {
+  const void* f_t;      // post-collision state at t, [nblocks][27][512] (compute type)
+  const void* lam_in;   // lambda_{t+1}, same layout
+  void* lam_out;        // lambda_t
+  void* dLdF;           // [3][nblocks*512] accumulator (compute type)
+  const double* force;  // [3][nblocks*512] or nullptr
+  int BX, BY, BZ, nblocks;
+  double omega;
+};
+cudaError_t launch_adjoint(int storage, const AdjointArgs& a, cudaStream_t st);
 
 struct ReduceArgs {
   const void* f;

@@ -92,6 +92,18 @@ __global__ void k_slab(const SlabArgs a) {
       a.out[3 * n + t] = uz;
       return;
     }
+    case SLAB_SET_LAMBDA: {
+      if (j < 0) return;
+      T* r = reinterpret_cast<T*>(a.raw) + blk * Q * kCells + cell;
+      for (int i = 0; i < Q; ++i) r[i * kCells] = T(a.in[int64_t(i) * n + t]);
+      return;
+    }
+    case SLAB_GET_FIELD3: {
+      const int64_t nn = int64_t(a.BX) * a.BY * a.BZ * kCells;
+      const T* r = reinterpret_cast<const T*>(a.raw);
+      for (int c = 0; c < 3; ++c) a.out[c * n + t] = j < 0 ? nan : double(r[c * nn + j]);
+      return;
+    }
     case SLAB_SET_FORCE: {
       if (j < 0) return;
       const int64_t nn = int64_t(a.BX) * a.BY * a.BZ * kCells;

@@ -23,7 +23,7 @@ EXPORTED = ["lbm_plan", "lbm_create", "lbm_create_error", "lbm_set_inflow", "lbm
             "lbm_set_force", "lbm_step", "lbm_sync", "lbm_macroscopic", "lbm_mass_momentum",
             "lbm_get_state", "lbm_set_state", "lbm_get_cells", "lbm_get_step", "lbm_set_step",
             "lbm_set_profiling", "lbm_get_profile", "lbm_get_tuning", "lbm_last_error", "lbm_destroy",
-            "lbm_mass_momentum_noalloc"]
+            "lbm_mass_momentum_noalloc", "lbm_adjoint_forward", "lbm_adjoint_backward"]
 NOALLOC_MAX_BLOCKS = 65536
 
 
@@ -80,6 +80,8 @@ def load():
         "lbm_last_error": (c_char_p, [c_void_p]),
         "lbm_destroy": (None, [c_void_p]),
         "lbm_mass_momentum_noalloc": (c_int, [c_int, c_int, c_void_p, c_int64, c_void_p, c_void_p]),
+        "lbm_adjoint_forward": (c_int, [c_void_p, c_int, c_int]),
+        "lbm_adjoint_backward": (c_int, [c_void_p, D, D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -234,6 +236,19 @@ def lbm_get_profile(ctx):
     n = (c_int64 * 5)()
     _check(ctx, load().lbm_get_profile(ctx.h, _dptr(ms), n))
     return ms, np.array(list(n), dtype=np.int64)
+
+
+def lbm_adjoint_forward(ctx, T, checkpoint_every):
+    _check(ctx, load().lbm_adjoint_forward(ctx.h, int(T), int(checkpoint_every)))
+
+
+def lbm_adjoint_backward(ctx, dLdf_T):
+    """dL/dF (3, NZ, NY, NX) from dL/df_T (27, NZ, NY, NX)."""
+    NX, NY, NZ = ctx.dims(0)
+    g = _f64(dLdf_T)
+    out = np.empty((3, NZ, NY, NX))
+    _check(ctx, load().lbm_adjoint_backward(ctx.h, _dptr(g), _dptr(out)))
+    return out
 
 
 def lbm_get_tuning(ctx):
