@@ -308,6 +308,125 @@ __device__ __forceinline__ void collide27(T* g, T omega, T Fx, T Fy, T Fz) {
   from_cube(v, g);
 }
 
+// The same collision in closed form, used by the stream-collide kernel.
+// Because every moment above second order is relaxed with rate 1, only the
+// six pre-collision second-order central moments matter; they follow from
+// raw sums: rho kappa_aa = S_aa - 2 u_a j_a + u_a^2 rho (+ const), rho kappa_ab =
+// S_ab - u_a j_b - u_b j_a + u_a u_b rho.  The post-collision normalised
+// central moments are then a sum of per-axis products: prod_a (1, 0, X_a)
+// for the diagonal part (X_a = 1/3 + D_a), plus kappa'_xy (0,1,0)(0,1,0)(1,0,Z)
+// and its two permutations, plus F/(2 rho) in the first order.  The 1-D
+// inverse transform of (1, 0, X) is phi(0) = 1 - u^2 - X, phi(+-1) =
+// (u^2 +- u + X)/2; of (0, 1, 0) psi(0) = -2u, psi(+-1) = u +- 1/2; of
+// (1, 0, 0) chi(0) = 1 - u^2, chi(+-1) = (u^2 +- u)/2.  Writing phi = w1 + delta
+// keeps f* - w free of cancellation:
+//   f*_i - w_i = drho W_i + rho (dx Py Pz... expanded) + k_xy psi_x psi_y phi_z + ...
+// (the paper notes that fixed rates remove most of the FCLB flops).
+template <class T, bool Force>
+__device__ __forceinline__ void collide27_closed(T* g, T omega, T Fx, T Fy, T Fz) {
+  // ---- zeroth, first and second raw moments of g by a z, y, x collapse
+  T m0[3][3], dz[3][3], sz[3][3];  // per (ex, ey): sum, difference, sum of ends along z
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const T lo = g[D3Q27::index(a - 1, b - 1, -1)];
+      const T mi = g[D3Q27::index(a - 1, b - 1, 0)];
+      const T hi = g[D3Q27::index(a - 1, b - 1, 1)];
+      sz[a][b] = hi + lo;
+      dz[a][b] = hi - lo;
+      m0[a][b] = sz[a][b] + mi;
+    }
+  T M0[3], My[3], Myy[3], Dz[3], Dyz[3], Szz[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const T e = m0[a][2] + m0[a][0];
+    Myy[a] = e;
+    My[a] = m0[a][2] - m0[a][0];
+    M0[a] = e + m0[a][1];
+    Dz[a] = dz[a][0] + dz[a][1] + dz[a][2];
+    Dyz[a] = dz[a][2] - dz[a][0];
+    Szz[a] = sz[a][0] + sz[a][1] + sz[a][2];
+  }
+  const T Sxx = M0[2] + M0[0];
+  const T drho = Sxx + M0[1];
+  const T jx = M0[2] - M0[0];
+  const T jy = My[0] + My[1] + My[2];
+  const T Sxy = My[2] - My[0];
+  const T Syy = Myy[0] + Myy[1] + Myy[2];
+  const T jz = Dz[0] + Dz[1] + Dz[2];
+  const T Sxz = Dz[2] - Dz[0];
+  const T Syz = Dyz[0] + Dyz[1] + Dyz[2];
+  const T Szzt = Szz[0] + Szz[1] + Szz[2];
+  // ---- velocity and second-order central moments (deviations from rho/3)
+  const T rho = T(1) + drho;
+  const T r = T(1) / rho;
+  T px = jx, py = jy, pz = jz;
+  if constexpr (Force) {
+    px += T(0.5) * Fx;
+    py += T(0.5) * Fy;
+    pz += T(0.5) * Fz;
+  }
+  const T ux = px * r, uy = py * r, uz = pz * r;
+  // rho u_a u_a - 2 u_a j_a = u_a (rho u_a - 2 j_a) = u_a (p_a - 2 j_a)
+  const T vxx = Sxx + ux * (px - T(2) * jx);
+  const T vyy = Syy + uy * (py - T(2) * jy);
+  const T vzz = Szzt + uz * (pz - T(2) * jz);
+  const T vxy = Sxy + ux * py - ux * jy - uy * jx;
+  const T vxz = Sxz + ux * pz - ux * jz - uz * jx;
+  const T vyz = Syz + uy * pz - uy * jz - uz * jy;
+  // ---- relaxation: deviatoric part with omega, trace to equilibrium
+  const T om1 = T(1) - omega;
+  const T mean = (vxx + vyy + vzz) * T(1.0 / 3.0);
+  const T Dx = om1 * (vxx - mean) * r, Dy = om1 * (vyy - mean) * r, Dz_ = om1 * (vzz - mean) * r;
+  const T kxy = om1 * vxy, kxz = om1 * vxz, kyz = om1 * vyz;  // rho kappa'
+  // ---- per-axis factors, index 0/1/2 = velocity -1/0/+1
+  T dl[3][3], ph[3][3], ps[3][3], ch[3][3];
+  const T uu[3] = {ux, uy, uz};
+  const T DD[3] = {Dx, Dy, Dz_};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const T u = uu[a], u2 = u * u, D = DD[a];
+    dl[a][1] = -u2 - D;
+    dl[a][0] = T(0.5) * (u2 - u + D);
+    dl[a][2] = T(0.5) * (u2 + u + D);
+    ph[a][1] = T(2.0 / 3.0) + dl[a][1];
+    ph[a][0] = T(1.0 / 6.0) + dl[a][0];
+    ph[a][2] = T(1.0 / 6.0) + dl[a][2];
+    ps[a][1] = T(-2) * u;
+    ps[a][0] = u - T(0.5);
+    ps[a][2] = u + T(0.5);
+    if constexpr (Force) {
+      ch[a][1] = T(1) - u2;
+      ch[a][0] = T(0.5) * (u2 - u);
+      ch[a][2] = T(0.5) * (u2 + u);
+    }
+  }
+  // ---- per (e_y, e_z) pair, then per e_x
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T P = ph[1][b] * ph[2][c];                            // phi_y phi_z
+      const T Qd = T(w1(b)) * dl[2][c] + dl[1][b] * ph[2][c];     // phi_y phi_z - w1_y w1_z
+      const T rP = rho * P, rQ = rho * Qd;
+      const T R = kxy * ps[1][b] * ph[2][c] + kxz * ph[1][b] * ps[2][c];
+      const T Sy = kyz * ps[1][b] * ps[2][c];
+      T Fp = T(0), Gp = T(0);
+      if constexpr (Force) {
+        Fp = T(0.5) * Fx * ch[1][b] * ch[2][c];
+        Gp = T(0.5) * Fy * ps[1][b] * ch[2][c] + T(0.5) * Fz * ch[1][b] * ps[2][c];
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const T W = T(w1(a) * w1(b) * w1(c));
+        T v = drho * W + dl[0][a] * rP + T(w1(a)) * rQ + ps[0][a] * R + ph[0][a] * Sy;
+        if constexpr (Force) v += ps[0][a] * Fp + ch[0][a] * Gp;
+        g[D3Q27::index(a - 1, b - 1, c - 1)] = v;
+      }
+    }
+}
+
 // Product-form D3Q27 equilibrium minus the weights: the distribution whose
 // normalised central moments are the Table 2 equilibria at rest shape.  Built
 // with the same inverse transform from the deviations drho * C_abc.

@@ -71,15 +71,13 @@ __global__ void __launch_bounds__(TPB) k_update(const UpdateArgs a) {
         const T S_ = collide19<T>(g, tau0, T(a.cs2_18));
         if (L.aux_dst) reinterpret_cast<T*>(L.aux_dst)[int64_t(w.block) * kCells + c] = S_;
       } else {
-        T Fx = T(0), Fy = T(0), Fz = T(0);
         if (a.force != nullptr && w.level == 0) {
           const int64_t n = int64_t(L.BX) * L.BY * L.BZ * kCells;
           const int64_t j = int64_t(w.block) * kCells + c;
-          Fx = T(a.force[j]);
-          Fy = T(a.force[n + j]);
-          Fz = T(a.force[2 * n + j]);
+          collide27_closed<T, true>(g, T(1) / tau0, T(a.force[j]), T(a.force[n + j]), T(a.force[2 * n + j]));
+        } else {
+          collide27_closed<T, false>(g, T(1) / tau0, T(0), T(0), T(0));
         }
-        collide27<T>(g, T(1) / tau0, Fx, Fy, Fz);
       }
       S* q = dst + c;
       static_for<Q>([&](auto i) { St::template put<Q, i>(q + int(i) * kCells, g[i]); });
