@@ -195,9 +195,9 @@ def run_uniform(lbm, torch, model, storage, field, steps, warmup, stream, sample
     lbm.lbm_step(ctx, prof_steps)
     pms, pn = lbm.lbm_get_profile(ctx)
     lbm.lbm_set_profiling(ctx, False)
-    threads, ctas = lbm.lbm_get_tuning(ctx)
+    threads, minb, ctas = lbm.lbm_get_tuning(ctx)
     out = dict(ctx=ctx, ms=ms, clocks=clocks, kernel_ms=pms[0] / max(pn[0], 1),
-               launches_per_step=int(pn.sum()) // prof_steps, tuning=(threads, ctas),
+               launches_per_step=int(pn.sum()) // prof_steps, tuning=(threads, minb, ctas),
                cells=N_GRID ** 3)
     return out
 
@@ -248,6 +248,42 @@ def run_jet(lbm, torch, model, steps, warmup, stream):
             "profile_ms_per_coarse_step": {k: round(float(v) / 3, 4) for k, v in
                                            zip(["update", "c2f", "f2c", "bc", "other"], pms)},
             "launches_per_coarse_step": int(pn.sum()) // 3}
+
+
+def run_jet3(lbm, torch, storage, steps, warmup, stream):
+    """3-level jet at the paper's scale (coarse 512x256x256, nozzle D = 32,
+    rings along the shear layer, 40.09 M active cells), D3Q27 FCLB."""
+    import synth
+    flags, centre = synth.jet_paper_scale()
+    nu_c = 0.05 * 32 / 1e4
+    ctx = lbm.lbm_create("d3q27", storage, (64, 32, 32), False, flags, 1.0 / (3 * nu_c + 0.5), 0.0,
+                         stream.cuda_stream)
+    lbm.lbm_set_inflow(ctx, centre[0], centre[1], 32.0, 0.05, 0.01, 5120)
+    info = lbm.lbm_plan((64, 32, 32), False, flags, "d3q27", storage)
+    lbm.lbm_step(ctx, warmup)
+    lbm.lbm_sync(ctx)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lbm.lbm_step(ctx, steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    lbm.lbm_set_profiling(ctx, True)
+    lbm.lbm_step(ctx, 2)
+    pms, pn = lbm.lbm_get_profile(ctx)
+    m = lbm.lbm_mass_momentum(ctx)
+    lbm.lbm_destroy(ctx)
+    upd = info.active_updates_per_coarse_step
+    peak, _ = measured_peak()
+    bpu = BYTES_PER_UPDATE[("d3q27", storage)]
+    return {"mlups": round(upd / (ms * 1e-3) / 1e6, 1), "ms_per_coarse_step": round(ms, 4),
+            "active_cells": [int(info.active_cells[l]) for l in range(3)],
+            "active_updates_per_coarse_step": int(upd), "steps": steps,
+            "frac_of_hbm_roofline": round(bpu * upd / (ms * 1e-3) / 1e9 / peak, 4),
+            "profile_ms_per_coarse_step": {k: round(float(v) / 2, 4) for k, v in
+                                           zip(["update", "c2f", "f2c", "bc", "other"], pms)},
+            "launches_per_coarse_step": int(pn.sum()) // 2, "final_momentum_x": float(m[1])}
 
 
 def run_adjoint(lbm, torch, stream, T=256, every=16, N=96):
@@ -330,7 +366,8 @@ def ours(args):
     K, W = args.steps, args.warmup
 
     if args.kernel_only:
-        r = run_uniform(lbm, torch, "d3q27", "f32", field, K, W, stream)
+        model, storage = args.variant.split("_")
+        r = run_uniform(lbm, torch, model, storage, field, K, W, stream)
         lbm.lbm_destroy(r["ctx"])
         if rank == 0:
             print(json.dumps({"kernel_only": True, "ms_per_step": r["ms"] / K,
@@ -410,6 +447,8 @@ def ours(args):
             lbm.lbm_destroy(r["ctx"])
         for model in ("d3q27", "d3q19"):
             variants["jet_2level_%s_f32" % model] = run_jet(lbm, torch, model, max(10, K // 4), 3, stream)
+        for storage in ("f32", "f16"):
+            variants["jet_3level_d3q27_%s" % storage] = run_jet3(lbm, torch, storage, max(20, K // 4), 3, stream)
         variants["adjoint_d3q27_f32"] = run_adjoint(lbm, torch, stream)
 
     line = {
@@ -420,7 +459,8 @@ def ours(args):
                                "(k^4 spectrum, k0=4, u_rms=0.04, nu=1e-4)",
                    "cells": cells, "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (1.81 GB per distribution buffer)",
-                   "launch": {"threads": head["tuning"][0], "ctas": head["tuning"][1]}},
+                   "launch": {"threads": head["tuning"][0], "min_ctas_per_sm": head["tuning"][1],
+                              "ctas": head["tuning"][2]}},
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": head["launches_per_step"] * K,
@@ -476,7 +516,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="headline only (no variants)")
     ap.add_argument("--kernel-only", action="store_true",
-                    help="only the headline stream-collide steps (for ncu captures)")
+                    help="only the stream-collide steps of one variant (for ncu captures)")
+    ap.add_argument("--variant", default="d3q27_f32",
+                    help="model_storage for --kernel-only, e.g. d3q19_f16")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -182,8 +182,9 @@ int lbm_set_profiling(lbm_ctx* ctx, int enable);
 int lbm_get_profile(lbm_ctx* ctx, double ms[5], int64_t launches[5]);
 
 /* Launch configuration of the stream-collide kernel chosen by the autotuner:
- * threads per CTA and CTAs per launch (0 = one CTA per block). */
-int lbm_get_tuning(const lbm_ctx* ctx, int* threads, int* ctas_per_sm);
+ * threads per CTA, the minimum resident CTAs per SM the kernel was compiled
+ * for (1 = no register cap), and CTAs per launch (0 = one CTA per block). */
+int lbm_get_tuning(const lbm_ctx* ctx, int* threads, int* min_ctas_per_sm, int* ctas);
 
 /* Mass/momentum audit for callers that cannot let the library allocate
  * device memory: code running under CUDA stream capture (allocation is not

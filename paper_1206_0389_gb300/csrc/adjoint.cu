@@ -123,39 +123,52 @@ __device__ __forceinline__ void fwd_x(T (&v)[3][3][3], T u, T uu) {
 
 // mu = J_C^T lambda for the pre-collision shifted values g; lam holds lambda
 // on entry and mu on exit; F-bar (dL/dF of this step) is added to Fb.
+// The relaxation only reads the six second-order central moments of the
+// incoming populations, v_aa = S_aa + u_a (p_a - 2 j_a) and
+// v_ab = S_ab + u_a p_b - u_a j_b - u_b j_a (S = raw second moments of g,
+// j = first moments, p = j + F/2 = rho u), so the forward transform is
+// reversed through those closed forms; the inverse passes and the relaxation
+// are reversed pass by pass.
 template <class T>
 __device__ __forceinline__ void collide27_adjoint(const T* g, T* lam, T omega, T Fx, T Fy, T Fz, T& Fbx,
                                                   T& Fby, T& Fbz) {
-  // ---- forward recomputation
-  T drho, jx, jy, jz;
-  moments27(g, drho, jx, jy, jz);
+  // ---- forward recomputation: raw moments, velocity, second-order central moments
+  T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
+  T Sxx = T(0), Syy = T(0), Szz = T(0), Sxy = T(0), Sxz = T(0), Syz = T(0);
+  static_for<27>([&](auto i) {
+    constexpr int x = D3Q27::ex(i), y = D3Q27::ey(i), z = D3Q27::ez(i);
+    const T v = g[i];
+    drho += v;
+    if constexpr (x != 0) { jx += T(x) * v; Sxx += v; }
+    if constexpr (y != 0) { jy += T(y) * v; Syy += v; }
+    if constexpr (z != 0) { jz += T(z) * v; Szz += v; }
+    if constexpr (x * y != 0) Sxy += T(x * y) * v;
+    if constexpr (x * z != 0) Sxz += T(x * z) * v;
+    if constexpr (y * z != 0) Syz += T(y * z) * v;
+  });
   const T r = T(1) / (T(1) + drho);
   const T px = jx + T(0.5) * Fx, py = jy + T(0.5) * Fy, pz = jz + T(0.5) * Fz;
   const T ux = px * r, uy = py * r, uz = pz * r;
   const T ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
-  T G[3][3][3], W[3][3][3], L[3][3][3];
-  to_cube(g, G);
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) W[a][b][c] = G[a][b][c];
-  forward27(W, ux, uy, uz);
+  const T vxx = Sxx + ux * (px - T(2) * jx), vyy = Syy + uy * (py - T(2) * jy), vzz = Szz + uz * (pz - T(2) * jz);
+  const T vxy = Sxy + ux * py - ux * jy - uy * jx;
+  const T vxz = Sxz + ux * pz - ux * jz - uz * jx;
+  const T vyz = Syz + uy * pz - uy * jz - uz * jy;
   const T om1 = T(1) - omega;
-  const T mean = (W[2][0][0] + W[0][2][0] + W[0][0][2]) * T(1.0 / 3.0);
+  const T mean = (vxx + vyy + vzz) * T(1.0 / 3.0);
   RelaxState<T> s;
   s.drho = drho;
   s.r = r;
-  s.A = om1 * (W[2][0][0] - mean);
-  s.B = om1 * (W[0][2][0] - mean);
-  s.C = om1 * (W[0][0][2] - mean);
-  s.kxy = om1 * W[1][1][0];
-  s.kxz = om1 * W[1][0][1];
-  s.kyz = om1 * W[0][1][1];
+  s.A = om1 * (vxx - mean);
+  s.B = om1 * (vyy - mean);
+  s.C = om1 * (vzz - mean);
+  s.kxy = om1 * vxy;
+  s.kxz = om1 * vxz;
+  s.kyz = om1 * vyz;
   s.Fx = Fx;
   s.Fy = Fy;
   s.Fz = Fz;
+  T W[3][3][3], L[3][3][3];
   to_cube(lam, L);
   T ubx = T(0), uby = T(0), ubz = T(0);
   // ---- inverse z pass (input = yinv(xinv(V')))
@@ -206,67 +219,41 @@ __device__ __forceinline__ void collide27_adjoint(const T* g, T* lam, T omega, T
          L[1][2][1] * B * s.kxz + L[1][1][2] * C * s.kxy +
          L[2][2][2] * ((A * B + A * C + B * C) * third + T(2) * A * B * C * r);
   const T Sb = (Ab + Bb + Cb) * third;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) L[a][b][c] = T(0);
-  L[2][0][0] = om1 * (Ab - Sb);
-  L[0][2][0] = om1 * (Bb - Sb);
-  L[0][0][2] = om1 * (Cb - Sb);
-  L[1][1][0] = om1 * kxyb;
-  L[1][0][1] = om1 * kxzb;
-  L[0][1][1] = om1 * kyzb;
-  // ---- forward x pass (input = fwd_y(fwd_z(G)))
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) W[a][b][c] = G[a][b][c];
-  fwd_z(W, uz, uz2);
-  fwd_y(W, uy, uy2);
-#pragma unroll
-  for (int j = 0; j < 3; ++j)
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-      ubx += fwd_line_adj(W[0][j][k], W[1][j][k], W[2][j][k], L[0][j][k], L[1][j][k], L[2][j][k], ux, ux2,
-                          T(c1(j) * c1(k)));
-  // ---- forward y pass (input = fwd_z(G))
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) W[a][b][c] = G[a][b][c];
-  fwd_z(W, uz, uz2);
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-      uby += fwd_line_adj(W[i][0][k], W[i][1][k], W[i][2][k], L[i][0][k], L[i][1][k], L[i][2][k], uy, uy2,
-                          T(w1(i) * c1(k)));
-  // ---- forward z pass (input = G)
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      ubz += fwd_line_adj(G[i][j][0], G[i][j][1], G[i][j][2], L[i][j][0], L[i][j][1], L[i][j][2], uz, uz2,
-                          T(w1(i) * w1(j)));
-  // ---- u = (j + F/2) r, r = 1/(1 + drho), drho = sum g, j = sum g e
-  const T jbx = ubx * r, jby = uby * r, jbz = ubz * r;
-  Fbx += T(0.5) * jbx;
-  Fby += T(0.5) * jby;
-  Fbz += T(0.5) * jbz;
+  const T vxxb = om1 * (Ab - Sb), vyyb = om1 * (Bb - Sb), vzzb = om1 * (Cb - Sb);
+  const T vxyb = om1 * kxyb, vxzb = om1 * kxzb, vyzb = om1 * kyzb;
+  // ---- second-order central moments from raw moments
+  T jbx = T(-2) * vxxb * ux - vxyb * uy - vxzb * uz;
+  T jby = T(-2) * vyyb * uy - vxyb * ux - vyzb * uz;
+  T jbz = T(-2) * vzzb * uz - vxzb * ux - vyzb * uy;
+  // (v_ab is written with u_a p_b, so p_x enters only v_xx and p_y only v_yy, v_xy)
+  T pbx = vxxb * ux;
+  T pby = vyyb * uy + vxyb * ux;
+  T pbz = vzzb * uz + vxzb * ux + vyzb * uy;
+  ubx += vxxb * (px - T(2) * jx) + vxyb * (py - jy) + vxzb * (pz - jz);
+  uby += vyyb * (py - T(2) * jy) + vxyb * (-jx) + vyzb * (pz - jz);
+  ubz += vzzb * (pz - T(2) * jz) + vxzb * (-jx) + vyzb * (-jy);
+  // ---- u = p r, p = j + F/2, r = 1/(1 + drho)
+  pbx += ubx * r;
+  pby += uby * r;
+  pbz += ubz * r;
   rb += ubx * px + uby * py + ubz * pz;
+  jbx += pbx;
+  jby += pby;
+  jbz += pbz;
+  Fbx += T(0.5) * pbx;
+  Fby += T(0.5) * pby;
+  Fbz += T(0.5) * pbz;
   drb -= rb * r * r;
-  from_cube(L, lam);
+  // ---- back to the populations: d/dg_i of (drho, j, S)
   static_for<27>([&](auto i) {
-    T m = lam[i] + drb;
-    if constexpr (D3Q27::ex(i) != 0) m += T(D3Q27::ex(i)) * jbx;
-    if constexpr (D3Q27::ey(i) != 0) m += T(D3Q27::ey(i)) * jby;
-    if constexpr (D3Q27::ez(i) != 0) m += T(D3Q27::ez(i)) * jbz;
+    constexpr int x = D3Q27::ex(i), y = D3Q27::ey(i), z = D3Q27::ez(i);
+    T m = drb;
+    if constexpr (x != 0) m += T(x) * jbx + vxxb;
+    if constexpr (y != 0) m += T(y) * jby + vyyb;
+    if constexpr (z != 0) m += T(z) * jbz + vzzb;
+    if constexpr (x * y != 0) m += T(x * y) * vxyb;
+    if constexpr (x * z != 0) m += T(x * z) * vxzb;
+    if constexpr (y * z != 0) m += T(y * z) * vyzb;
     lam[i] = m;
   });
 }

@@ -76,7 +76,7 @@ struct lbm_ctx {
   double y0 = 0, z0 = 0, diameter = 0, u_in = 0, perturb = 0;
   uint64_t seed = 0;
   // launch configuration
-  int threads = 256, ctas = 0;
+  int threads = 256, minb = 1, ctas = 0;
   // graphs, one per level-0 parity
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graphs_valid = false;
@@ -263,7 +263,7 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
 
 cudaError_t run_op(lbm_ctx* c, const Op& op) {
   switch (op.kind) {
-    case Op::UPDATE: return launch_update(c->model, c->storage, op.ua, c->threads, c->ctas, c->stream);
+    case Op::UPDATE: return launch_update(c->model, c->storage, op.ua, c->threads, c->minb, c->ctas, c->stream);
     case Op::C2F: return launch_c2f(c->model, c->storage, op.ca, c->stream);
     case Op::F2C: return launch_f2c(c->model, c->storage, op.fa, c->stream);
     case Op::BC: return launch_bc(c->model, c->storage, op.ba, c->stream);
@@ -347,16 +347,17 @@ int autotune(lbm_ctx* ctx) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int bt = 256, bc = 0;
-  const int tlist[3] = {128, 256, 512};
-  for (int t : tlist) {
+  int bt = 256, bm = 1, bc = 0;
+  const int shapes[5][2] = {{128, 1}, {256, 1}, {512, 1}, {128, 8}, {256, 4}};
+  for (const auto& sh : shapes) {
+    const int t = sh[0], mb = sh[1];
     int occ = 0;
-    if (update_occupancy(ctx->model, ctx->storage, t, &occ) != cudaSuccess || occ < 1) continue;
+    if (update_occupancy(ctx->model, ctx->storage, t, mb, &occ) != cudaSuccess || occ < 1) continue;
     const int clist[2] = {0, occ * ctx->sms};
     for (int cc : clist) {
-      if (launch_update(ctx->model, ctx->storage, big->ua, t, cc, ctx->stream) != cudaSuccess) continue;
+      if (launch_update(ctx->model, ctx->storage, big->ua, t, mb, cc, ctx->stream) != cudaSuccess) continue;
       CK(cudaEventRecord(e0, ctx->stream));
-      for (int r = 0; r < 3; ++r) CK(launch_update(ctx->model, ctx->storage, big->ua, t, cc, ctx->stream));
+      for (int r = 0; r < 3; ++r) CK(launch_update(ctx->model, ctx->storage, big->ua, t, mb, cc, ctx->stream));
       CK(cudaEventRecord(e1, ctx->stream));
       CK(cudaEventSynchronize(e1));
       float ms = 0;
@@ -364,6 +365,7 @@ int autotune(lbm_ctx* ctx) {
       if (ms < best) {
         best = ms;
         bt = t;
+        bm = mb;
         bc = cc;
       }
     }
@@ -371,6 +373,7 @@ int autotune(lbm_ctx* ctx) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ctx->threads = bt;
+  ctx->minb = bm;
   ctx->ctas = bc;
   return LBM_OK;
 }
@@ -946,7 +949,7 @@ int lbm_adjoint_backward(lbm_ctx* ctx, const double* dLdf_T, double* dLdF) {
     for (int k = 0; k + 1 < m; ++k) {
       ua.lv[0].src = seg(k);
       ua.lv[0].dst = seg(k + 1);
-      CK(launch_update(ctx->model, ctx->storage, ua, ctx->threads, ctx->ctas, ctx->stream));
+      CK(launch_update(ctx->model, ctx->storage, ua, ctx->threads, ctx->minb, ctx->ctas, ctx->stream));
     }
     for (int k = m - 1; k >= 0; --k) {
       aa.f_t = seg(k);
@@ -970,9 +973,10 @@ int lbm_adjoint_backward(lbm_ctx* ctx, const double* dLdf_T, double* dLdF) {
   return slab_transfer(ctx, 0, SLAB_GET_FIELD3, nullptr, hout, 3, nullptr, ctx->adj_gF);
 }
 
-int lbm_get_tuning(const lbm_ctx* ctx, int* threads, int* ctas) {
-  if (!ctx || !threads || !ctas) return LBM_ERR_ARG;
+int lbm_get_tuning(const lbm_ctx* ctx, int* threads, int* min_ctas_per_sm, int* ctas) {
+  if (!ctx || !threads || !min_ctas_per_sm || !ctas) return LBM_ERR_ARG;
   *threads = ctx->threads;
+  *min_ctas_per_sm = ctx->minb;
   *ctas = ctx->ctas;
   return LBM_OK;
 }

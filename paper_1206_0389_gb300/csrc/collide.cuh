@@ -428,19 +428,35 @@ __device__ __forceinline__ void collide27_closed(T* g, T omega, T Fx, T Fy, T Fz
 }
 
 // Product-form D3Q27 equilibrium minus the weights: the distribution whose
-// normalised central moments are the Table 2 equilibria at rest shape.  Built
-// with the same inverse transform from the deviations drho * C_abc.
+// normalised central moments are the Table 2 equilibria at rest shape is
+// rho prod_a phi(e_a, u_a), phi(0) = 2/3 - u^2, phi(+-1) = (1/3 + u^2 +- u)/2.
+// With phi = w1 + delta it is evaluated without cancellation as
+// drho W + rho (delta_x phi_y phi_z + w1_x (delta_y phi_z + w1_y delta_z)).
 template <class T>
 __device__ __forceinline__ void feq27(T drho, T ux, T uy, T uz, T* out) {
-  T v[3][3][3];
+  const T rho = T(1) + drho;
+  T dl[3][3], ph[3][3];
+  const T uu[3] = {ux, uy, uz};
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int a = 0; a < 3; ++a) {
+    const T u = uu[a], u2 = u * u;
+    dl[a][1] = -u2;
+    dl[a][0] = T(0.5) * (u2 - u);
+    dl[a][2] = T(0.5) * (u2 + u);
+    ph[a][1] = T(2.0 / 3.0) + dl[a][1];
+    ph[a][0] = T(1.0 / 6.0) + dl[a][0];
+    ph[a][2] = T(1.0 / 6.0) + dl[a][2];
+  }
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
+  for (int b = 0; b < 3; ++b)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) v[a][b][c] = drho * T(c1(a) * c1(b) * c1(c));
-  inverse27(v, ux, uy, uz);
-  from_cube(v, out);
+    for (int c = 0; c < 3; ++c) {
+      const T rP = rho * ph[1][b] * ph[2][c];
+      const T rQ = rho * (T(w1(b)) * dl[2][c] + dl[1][b] * ph[2][c]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        out[D3Q27::index(a - 1, b - 1, c - 1)] = drho * T(w1(a) * w1(b) * w1(c)) + dl[0][a] * rP + T(w1(a)) * rQ;
+    }
 }
 
 // ------------------------------------------------------------------ model traits

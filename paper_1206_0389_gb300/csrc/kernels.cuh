@@ -116,9 +116,9 @@ struct BCArgs {
 
 // ------------------------------------------------------------------ launchers
 // model: 0 D3Q19 MRT-LES, 1 D3Q27 FCLB; storage: lbm_storage.
-cudaError_t launch_update(int model, int storage, const UpdateArgs& a, int threads, int ctas,
+cudaError_t launch_update(int model, int storage, const UpdateArgs& a, int threads, int minb, int ctas,
                           cudaStream_t st);
-cudaError_t update_occupancy(int model, int storage, int threads, int* ctas_per_sm);
+cudaError_t update_occupancy(int model, int storage, int threads, int minb, int* ctas_per_sm);
 cudaError_t launch_c2f(int model, int storage, const C2FArgs& a, cudaStream_t st);
 cudaError_t launch_f2c(int model, int storage, const F2CArgs& a, cudaStream_t st);
 cudaError_t launch_bc(int model, int storage, const BCArgs& a, cudaStream_t st);

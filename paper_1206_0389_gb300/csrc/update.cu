@@ -20,8 +20,8 @@
 
 namespace lbm {
 
-template <class M, class S, int TPB>
-__global__ void __launch_bounds__(TPB) k_update(const UpdateArgs a) {
+template <class M, class S, int TPB, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
   using St = Store<S>;
   using T = typename St::T;
   constexpr int Q = M::Q;
@@ -85,50 +85,53 @@ __global__ void __launch_bounds__(TPB) k_update(const UpdateArgs a) {
   }
 }
 
+// Launch shapes the autotuner chooses from: threads per CTA, and a minimum
+// number of resident CTAs per SM that caps the registers (higher occupancy
+// for the FP16 variants, whose half-size loads keep fewer bytes in flight).
 template <class M, class S>
-static cudaError_t launch_ms(const UpdateArgs& a, int threads, int ctas, cudaStream_t st) {
+static cudaError_t launch_ms(const UpdateArgs& a, int threads, int minb, int ctas, cudaStream_t st) {
   if (a.nitems == 0) return cudaSuccess;
   const int grid = ctas > 0 ? std::min(ctas, a.nitems) : a.nitems;
-  switch (threads) {
-    case 128: k_update<M, S, 128><<<grid, 128, 0, st>>>(a); break;
-    case 256: k_update<M, S, 256><<<grid, 256, 0, st>>>(a); break;
-    case 512: k_update<M, S, 512><<<grid, 512, 0, st>>>(a); break;
-    default: return cudaErrorInvalidValue;
-  }
+  if (threads == 128 && minb == 1) k_update<M, S, 128, 1><<<grid, 128, 0, st>>>(a);
+  else if (threads == 256 && minb == 1) k_update<M, S, 256, 1><<<grid, 256, 0, st>>>(a);
+  else if (threads == 512 && minb == 1) k_update<M, S, 512, 1><<<grid, 512, 0, st>>>(a);
+  else if (threads == 128 && minb == 8) k_update<M, S, 128, 8><<<grid, 128, 0, st>>>(a);
+  else if (threads == 256 && minb == 4) k_update<M, S, 256, 4><<<grid, 256, 0, st>>>(a);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
 template <class M, class S>
-static cudaError_t occ_ms(int threads, int* n) {
-  switch (threads) {
-    case 128: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128>, 128, 0);
-    case 256: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 256>, 256, 0);
-    case 512: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 512>, 512, 0);
-    default: return cudaErrorInvalidValue;
-  }
+static cudaError_t occ_ms(int threads, int minb, int* n) {
+  if (threads == 128 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 1>, 128, 0);
+  if (threads == 256 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 256, 1>, 256, 0);
+  if (threads == 512 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 512, 1>, 512, 0);
+  if (threads == 128 && minb == 8) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 8>, 128, 0);
+  if (threads == 256 && minb == 4) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 256, 4>, 256, 0);
+  return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_update(int model, int storage, const UpdateArgs& a, int threads, int ctas,
+cudaError_t launch_update(int model, int storage, const UpdateArgs& a, int threads, int minb, int ctas,
                           cudaStream_t st) {
   if (model == LBM_D3Q19_MRT_LES) {
-    if (storage == LBM_F64) return launch_ms<MrtLes, double>(a, threads, ctas, st);
-    if (storage == LBM_F32) return launch_ms<MrtLes, float>(a, threads, ctas, st);
-    return launch_ms<MrtLes, __half>(a, threads, ctas, st);
+    if (storage == LBM_F64) return launch_ms<MrtLes, double>(a, threads, minb, ctas, st);
+    if (storage == LBM_F32) return launch_ms<MrtLes, float>(a, threads, minb, ctas, st);
+    return launch_ms<MrtLes, __half>(a, threads, minb, ctas, st);
   }
-  if (storage == LBM_F64) return launch_ms<Fclb, double>(a, threads, ctas, st);
-  if (storage == LBM_F32) return launch_ms<Fclb, float>(a, threads, ctas, st);
-  return launch_ms<Fclb, __half>(a, threads, ctas, st);
+  if (storage == LBM_F64) return launch_ms<Fclb, double>(a, threads, minb, ctas, st);
+  if (storage == LBM_F32) return launch_ms<Fclb, float>(a, threads, minb, ctas, st);
+  return launch_ms<Fclb, __half>(a, threads, minb, ctas, st);
 }
 
-cudaError_t update_occupancy(int model, int storage, int threads, int* n) {
+cudaError_t update_occupancy(int model, int storage, int threads, int minb, int* n) {
   if (model == LBM_D3Q19_MRT_LES) {
-    if (storage == LBM_F64) return occ_ms<MrtLes, double>(threads, n);
-    if (storage == LBM_F32) return occ_ms<MrtLes, float>(threads, n);
-    return occ_ms<MrtLes, __half>(threads, n);
+    if (storage == LBM_F64) return occ_ms<MrtLes, double>(threads, minb, n);
+    if (storage == LBM_F32) return occ_ms<MrtLes, float>(threads, minb, n);
+    return occ_ms<MrtLes, __half>(threads, minb, n);
   }
-  if (storage == LBM_F64) return occ_ms<Fclb, double>(threads, n);
-  if (storage == LBM_F32) return occ_ms<Fclb, float>(threads, n);
-  return occ_ms<Fclb, __half>(threads, n);
+  if (storage == LBM_F64) return occ_ms<Fclb, double>(threads, minb, n);
+  if (storage == LBM_F32) return occ_ms<Fclb, float>(threads, minb, n);
+  return occ_ms<Fclb, __half>(threads, minb, n);
 }
 
 }  // namespace lbm

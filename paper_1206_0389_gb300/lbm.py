@@ -76,7 +76,7 @@ def load():
         "lbm_set_step": (c_int, [c_void_p, c_int64]),
         "lbm_set_profiling": (c_int, [c_void_p, c_int]),
         "lbm_get_profile": (c_int, [c_void_p, D, P(c_int64)]),
-        "lbm_get_tuning": (c_int, [c_void_p, P(c_int), P(c_int)]),
+        "lbm_get_tuning": (c_int, [c_void_p, P(c_int), P(c_int), P(c_int)]),
         "lbm_last_error": (c_char_p, [c_void_p]),
         "lbm_destroy": (None, [c_void_p]),
         "lbm_mass_momentum_noalloc": (c_int, [c_int, c_int, c_void_p, c_int64, c_void_p, c_void_p]),
@@ -252,9 +252,10 @@ def lbm_adjoint_backward(ctx, dLdf_T):
 
 
 def lbm_get_tuning(ctx):
-    t, c = c_int(), c_int()
-    _check(ctx, load().lbm_get_tuning(ctx.h, ctypes.byref(t), ctypes.byref(c)))
-    return t.value, c.value
+    """(threads per CTA, min resident CTAs per SM compiled for, CTAs per launch or 0)."""
+    t, m, c = c_int(), c_int(), c_int()
+    _check(ctx, load().lbm_get_tuning(ctx.h, ctypes.byref(t), ctypes.byref(m), ctypes.byref(c)))
+    return t.value, m.value, c.value
 
 
 def lbm_last_error(ctx):
