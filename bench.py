@@ -42,7 +42,7 @@ OMEGA = 1.0 / (3.0 * NU + 0.5)
 BYTES_PER_UPDATE = {("d3q27", "f32"): 216, ("d3q27", "f16"): 108, ("d3q27", "f64"): 432,
                     ("d3q19", "f32"): 152, ("d3q19", "f16"): 76, ("d3q19", "f64"): 304}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "update_kernel_traffic.txt")
-KERNEL_SOURCES = ["paper_1206_0389_gb300/csrc/update.cu", "paper_1206_0389_gb300/csrc/collide.cuh",
+KERNEL_SOURCES = ["paper_1206_0389_gb300/csrc/update.cuh", "paper_1206_0389_gb300/csrc/collide.cuh",
                   "paper_1206_0389_gb300/csrc/lattice.cuh"]
 
 

@@ -11,7 +11,9 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "liblbm.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["update.cu", "interface.cu", "util.cu", "api.cu", "plan.cpp", "noalloc.cu", "adjoint.cu"]
+SOURCES = ["update.cu", "update_d3q19_f64.cu", "update_d3q19_f32.cu", "update_d3q19_f16.cu",
+           "update_d3q27_f64.cu", "update_d3q27_f32.cu", "update_d3q27_f16.cu",
+           "interface.cu", "util.cu", "api.cu", "plan.cpp", "noalloc.cu", "adjoint.cu"]
 
 
 def nvcc():

@@ -123,44 +123,61 @@ __device__ __forceinline__ void moments19(const T* g, T& drho, T& ux, T& uy, T& 
 // others: axis links receive 1/2 (Pi_aa - tr Pi / 3), the diagonal links of
 // plane ab receive 1/4 e_a e_b Pi_ab, the rest link 0.  s1 = 1/tau_total with
 // tau_total from Eq. eqTauTotFinal and Q from Eq. EqnQ.
+// Opposite links (2k-1, 2k) are handled as pairs: their sums carry the even
+// moments and their differences the odd ones, and since the D3Q19 set is
+// isotropic to fourth order, sum_i e_a e_b f_eq_i = drho/3 delta_ab + u_a u_b,
+// so Pi^neq = sum e e f - drho/3 I - u u without forming f - f_eq per link.
 // Returns |S| = 3 Q / (2 tau_total) (Eq. eqStrainRate, lattice units).
 template <class T>
 __device__ __forceinline__ T collide19(T* g, T tau0, T cs2_18) {
-  T drho, ux, uy, uz;
-  moments19(g, drho, ux, uy, uz);
-  T feq[19];
-  feq19(drho, ux, uy, uz, feq);
-  T pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
-  static_for<19>([&](auto i) {
-    constexpr int x = D3Q19::ex(i), y = D3Q19::ey(i), z = D3Q19::ez(i);
-    const T n = g[i] - feq[i];
-    g[i] = n;  // keep the non-equilibrium part
-    if constexpr (x != 0) pxx += n;
-    if constexpr (y != 0) pyy += n;
-    if constexpr (z != 0) pzz += n;
-    if constexpr (x * y != 0) pxy += T(x * y) * n;
-    if constexpr (x * z != 0) pxz += T(x * z) * n;
-    if constexpr (y * z != 0) pyz += T(y * z) * n;
+  T sp[9], dp[9];
+  static_for<9>([&](auto p) {
+    sp[p] = g[2 * p + 1] + g[2 * p + 2];
+    dp[p] = g[2 * p + 1] - g[2 * p + 2];
   });
-  const T qq = T(2) * (pxx * pxx + pyy * pyy + pzz * pzz +
-                       T(2) * (pxy * pxy + pxz * pxz + pyz * pyz));
+  T drho = g[0], ux = T(0), uy = T(0), uz = T(0);
+  T sxx = T(0), syy = T(0), szz = T(0), sxy = T(0), sxz = T(0), syz = T(0);
+  static_for<9>([&](auto p) {
+    constexpr int i = 2 * p + 1;
+    constexpr int x = D3Q19::ex(i), y = D3Q19::ey(i), z = D3Q19::ez(i);
+    drho += sp[p];
+    if constexpr (x != 0) { ux += T(x) * dp[p]; sxx += sp[p]; }
+    if constexpr (y != 0) { uy += T(y) * dp[p]; syy += sp[p]; }
+    if constexpr (z != 0) { uz += T(z) * dp[p]; szz += sp[p]; }
+    if constexpr (x * y != 0) sxy += T(x * y) * sp[p];
+    if constexpr (x * z != 0) sxz += T(x * z) * sp[p];
+    if constexpr (y * z != 0) syz += T(y * z) * sp[p];
+  });
+  const T d3 = drho * T(1.0 / 3.0);
+  const T pxx = sxx - d3 - ux * ux, pyy = syy - d3 - uy * uy, pzz = szz - d3 - uz * uz;
+  const T pxy = sxy - ux * uy, pxz = sxz - ux * uz, pyz = syz - uy * uz;
+  const T qq = T(2) * (pxx * pxx + pyy * pyy + pzz * pzz + T(2) * (pxy * pxy + pxz * pxz + pyz * pyz));
   const T Qn = sqrt(qq);
   const T tau = T(0.5) * (tau0 + sqrt(tau0 * tau0 + cs2_18 * Qn));
   const T k = T(1) - T(1) / tau;
   const T tr3 = (pxx + pyy + pzz) * T(1.0 / 3.0);
   const T ax = T(0.5) * k * (pxx - tr3), ay = T(0.5) * k * (pyy - tr3), az = T(0.5) * k * (pzz - tr3);
   const T dxy = T(0.25) * k * pxy, dxz = T(0.25) * k * pxz, dyz = T(0.25) * k * pyz;
-  static_for<19>([&](auto i) {
+  const T base = drho - T(1.5) * (ux * ux + uy * uy + uz * uz);
+  g[0] = T(D3Q19::w(0)) * base;
+  static_for<9>([&](auto p) {
+    constexpr int i = 2 * p + 1;
     constexpr int x = D3Q19::ex(i), y = D3Q19::ey(i), z = D3Q19::ez(i);
     constexpr int nz = (x != 0) + (y != 0) + (z != 0);
-    T p = T(0);
-    if constexpr (nz == 1) p = (x != 0) ? ax : (y != 0) ? ay : az;
-    if constexpr (nz == 2) {
-      if constexpr (z == 0) p = T(x * y) * dxy;
-      else if constexpr (y == 0) p = T(x * z) * dxz;
-      else p = T(y * z) * dyz;
-    }
-    g[i] = feq[i] + p;
+    T eu = T(0);
+    if constexpr (x != 0) eu += T(x) * ux;
+    if constexpr (y != 0) eu += T(y) * uy;
+    if constexpr (z != 0) eu += T(z) * uz;
+    constexpr T w = T(D3Q19::w(i));
+    T proj;
+    if constexpr (nz == 1) proj = (x != 0) ? ax : (y != 0) ? ay : az;
+    else if constexpr (z == 0) proj = T(x * y) * dxy;
+    else if constexpr (y == 0) proj = T(x * z) * dxz;
+    else proj = T(y * z) * dyz;
+    const T sym = w * (base + T(4.5) * eu * eu) + proj;
+    const T asym = (T(3) * w) * eu;
+    g[i] = sym + asym;
+    g[i + 1] = sym - asym;
   });
   return T(1.5) * Qn / tau;
 }

@@ -34,7 +34,7 @@ __global__ void k_c2f(const C2FArgs a) {
   T Sh = T(0);
   const S* co = reinterpret_cast<const S*>(a.c_old);
   const S* cn = reinterpret_cast<const S*>(a.c_new);
-#pragma unroll 1
+#pragma unroll 2
   for (int k = 0; k < 8; ++k) {
     const T wx = (k & 1) ? tx : T(1) - tx;
     const T wy = (k & 2) ? ty : T(1) - ty;
@@ -78,7 +78,7 @@ __global__ void k_f2c(const F2CArgs a) {
   T acc[Q];
   static_for<Q>([&](auto i) { acc[i] = T(0); });
   T accS = T(0);
-#pragma unroll 1
+#pragma unroll 2
   for (int ch = 0; ch < 8; ++ch) {
     const int64_t base = int64_t(it.fblock[ch]) * QS + it.fcell[ch];
     T g[Q];

@@ -396,6 +396,11 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
           }
         }
     (void)dc;
+    // fine ghost cells that share a coarse stencil become neighbouring threads
+    std::stable_sort(f.c2f.begin(), f.c2f.end(), [](const C2FItem& a, const C2FItem& b) {
+      if (a.cblock[0] != b.cblock[0]) return a.cblock[0] < b.cblock[0];
+      return a.ccell[0] < b.ccell[0];
+    });
   }
   for (int l = 0; l + 1 < L; ++l) {
     LevelPlan& c = P.lv[l];

@@ -1,137 +1,31 @@
-// Fused pull-stream + collide kernel (one launch covers the work of every
-// level that takes a substep at that time).
-//
-// f(x, t+1) = f~(x - e_i, t) (the streaming on the left of Eqs. lbgk / MRT),
-// then the local collision of Section 2, then f~(x, t+1) is stored.
-// Storage per level: a dense box of 8^3 blocks, [block][i][512 cells], cell
-// index x + 8 y + 64 z.  A warp covers four x-rows of one block, so loads of
-// one population are 128-byte (F32) contiguous runs, shifted by one cell for
-// populations with e_x != 0.
-//
-// Neighbour blocks are found arithmetically in the level box: per thread the
-// extra element offset for leaving the block along -x is Xm (non-zero only
-// for cells with x == 0), along +x Xp (x == 7), likewise Ym/Yp/Zm/Zp, so the
-// source of population i is own_block + i*512 + cell - (e_x + 8 e_y + 64 e_z)
-// + X(e_x) + Y(e_y) + Z(e_z) with X(+1) = Xm, X(-1) = Xp, X(0) = 0.
-#include <algorithm>
-
-#include "collide.cuh"
-#include "kernels.cuh"
+// Dispatch of the fused stream-collide kernel (update.cuh) over model and
+// storage; each (model, storage) pair is compiled in its own translation unit
+// (update_<model>_<storage>.cu) so the build runs in parallel.
+#include "update.cuh"
 
 namespace lbm {
-
-template <class M, class S, int TPB, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
-  using St = Store<S>;
-  using T = typename St::T;
-  constexpr int Q = M::Q;
-  constexpr int QS = Q * kCells;
-  for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
-    const WorkItem w = a.items[it];
-    const LevelPtrs& L = a.lv[w.level];
-    const int BX = L.BX, BXY = L.BX * L.BY;
-    // block deltas towards -x, +x, -y, +y, -z, +z (periodic wrap on box faces)
-    const int dxm = (w.edges & 1) ? (L.BX - 1) : -1;
-    const int dxp = (w.edges & 2) ? -(L.BX - 1) : 1;
-    const int dym = (w.edges & 4) ? BX * (L.BY - 1) : -BX;
-    const int dyp = (w.edges & 8) ? -BX * (L.BY - 1) : BX;
-    const int dzm = (w.edges & 16) ? BXY * (L.BZ - 1) : -BXY;
-    const int dzp = (w.edges & 32) ? -BXY * (L.BZ - 1) : BXY;
-    const T tau0 = T(L.tau0);
-    const S* __restrict__ src = reinterpret_cast<const S*>(L.src) + int64_t(w.block) * QS;
-    S* __restrict__ dst = reinterpret_cast<S*>(L.dst) + int64_t(w.block) * QS;
-#pragma unroll 1
-    for (int c = threadIdx.x; c < kCells; c += TPB) {
-      if (w.mask >= 0) {
-        const uint32_t m = __ldg(a.masks + w.mask * 16 + (c >> 5));
-        if (!((m >> (c & 31)) & 1u)) continue;
-      }
-      const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
-      const int Xm = (x == 0) ? dxm * QS + 8 : 0;
-      const int Xp = (x == 7) ? dxp * QS - 8 : 0;
-      const int Ym = (y == 0) ? dym * QS + 64 : 0;
-      const int Yp = (y == 7) ? dyp * QS - 64 : 0;
-      const int Zm = (z == 0) ? dzm * QS + 512 : 0;
-      const int Zp = (z == 7) ? dzp * QS - 512 : 0;
-      const S* p = src + c;
-      T g[Q];
-      static_for<Q>([&](auto i) {
-        constexpr int ex = Lattice<Q>::ex(i), ey = Lattice<Q>::ey(i), ez = Lattice<Q>::ez(i);
-        constexpr int k = int(i) * kCells - (ex + 8 * ey + 64 * ez);
-        int o = 0;
-        if constexpr (ex == 1) o += Xm;
-        if constexpr (ex == -1) o += Xp;
-        if constexpr (ey == 1) o += Ym;
-        if constexpr (ey == -1) o += Yp;
-        if constexpr (ez == 1) o += Zm;
-        if constexpr (ez == -1) o += Zp;
-        g[i] = St::template get<Q, i>(p + o + k);
-      });
-      if constexpr (Q == 19) {
-        const T S_ = collide19<T>(g, tau0, T(a.cs2_18));
-        if (L.aux_dst) reinterpret_cast<T*>(L.aux_dst)[int64_t(w.block) * kCells + c] = S_;
-      } else {
-        if (a.force != nullptr && w.level == 0) {
-          const int64_t n = int64_t(L.BX) * L.BY * L.BZ * kCells;
-          const int64_t j = int64_t(w.block) * kCells + c;
-          collide27_closed<T, true>(g, T(1) / tau0, T(a.force[j]), T(a.force[n + j]), T(a.force[2 * n + j]));
-        } else {
-          collide27_closed<T, false>(g, T(1) / tau0, T(0), T(0), T(0));
-        }
-      }
-      S* q = dst + c;
-      static_for<Q>([&](auto i) { St::template put<Q, i>(q + int(i) * kCells, g[i]); });
-    }
-  }
-}
-
-// Launch shapes the autotuner chooses from: threads per CTA, and a minimum
-// number of resident CTAs per SM that caps the registers (higher occupancy
-// for the FP16 variants, whose half-size loads keep fewer bytes in flight).
-template <class M, class S>
-static cudaError_t launch_ms(const UpdateArgs& a, int threads, int minb, int ctas, cudaStream_t st) {
-  if (a.nitems == 0) return cudaSuccess;
-  const int grid = ctas > 0 ? std::min(ctas, a.nitems) : a.nitems;
-  if (threads == 128 && minb == 1) k_update<M, S, 128, 1><<<grid, 128, 0, st>>>(a);
-  else if (threads == 256 && minb == 1) k_update<M, S, 256, 1><<<grid, 256, 0, st>>>(a);
-  else if (threads == 512 && minb == 1) k_update<M, S, 512, 1><<<grid, 512, 0, st>>>(a);
-  else if (threads == 128 && minb == 8) k_update<M, S, 128, 8><<<grid, 128, 0, st>>>(a);
-  else if (threads == 256 && minb == 4) k_update<M, S, 256, 4><<<grid, 256, 0, st>>>(a);
-  else return cudaErrorInvalidValue;
-  return cudaGetLastError();
-}
-
-template <class M, class S>
-static cudaError_t occ_ms(int threads, int minb, int* n) {
-  if (threads == 128 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 1>, 128, 0);
-  if (threads == 256 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 256, 1>, 256, 0);
-  if (threads == 512 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 512, 1>, 512, 0);
-  if (threads == 128 && minb == 8) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 8>, 128, 0);
-  if (threads == 256 && minb == 4) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 256, 4>, 256, 0);
-  return cudaErrorInvalidValue;
-}
 
 cudaError_t launch_update(int model, int storage, const UpdateArgs& a, int threads, int minb, int ctas,
                           cudaStream_t st) {
   if (model == LBM_D3Q19_MRT_LES) {
-    if (storage == LBM_F64) return launch_ms<MrtLes, double>(a, threads, minb, ctas, st);
-    if (storage == LBM_F32) return launch_ms<MrtLes, float>(a, threads, minb, ctas, st);
-    return launch_ms<MrtLes, __half>(a, threads, minb, ctas, st);
+    if (storage == LBM_F64) return launch_update_d3q19_f64(a, threads, minb, ctas, st);
+    if (storage == LBM_F32) return launch_update_d3q19_f32(a, threads, minb, ctas, st);
+    return launch_update_d3q19_f16(a, threads, minb, ctas, st);
   }
-  if (storage == LBM_F64) return launch_ms<Fclb, double>(a, threads, minb, ctas, st);
-  if (storage == LBM_F32) return launch_ms<Fclb, float>(a, threads, minb, ctas, st);
-  return launch_ms<Fclb, __half>(a, threads, minb, ctas, st);
+  if (storage == LBM_F64) return launch_update_d3q27_f64(a, threads, minb, ctas, st);
+  if (storage == LBM_F32) return launch_update_d3q27_f32(a, threads, minb, ctas, st);
+  return launch_update_d3q27_f16(a, threads, minb, ctas, st);
 }
 
 cudaError_t update_occupancy(int model, int storage, int threads, int minb, int* n) {
   if (model == LBM_D3Q19_MRT_LES) {
-    if (storage == LBM_F64) return occ_ms<MrtLes, double>(threads, minb, n);
-    if (storage == LBM_F32) return occ_ms<MrtLes, float>(threads, minb, n);
-    return occ_ms<MrtLes, __half>(threads, minb, n);
+    if (storage == LBM_F64) return occupancy_update_d3q19_f64(threads, minb, n);
+    if (storage == LBM_F32) return occupancy_update_d3q19_f32(threads, minb, n);
+    return occupancy_update_d3q19_f16(threads, minb, n);
   }
-  if (storage == LBM_F64) return occ_ms<Fclb, double>(threads, minb, n);
-  if (storage == LBM_F32) return occ_ms<Fclb, float>(threads, minb, n);
-  return occ_ms<Fclb, __half>(threads, minb, n);
+  if (storage == LBM_F64) return occupancy_update_d3q27_f64(threads, minb, n);
+  if (storage == LBM_F32) return occupancy_update_d3q27_f32(threads, minb, n);
+  return occupancy_update_d3q27_f16(threads, minb, n);
 }
 
 }  // namespace lbm
