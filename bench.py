@@ -365,6 +365,25 @@ def ours(args):
     field = synth.spectrum_field(N_GRID, seed=1206 + rank)
     K, W = args.steps, args.warmup
 
+    if args.kernel_only and args.variant.startswith("jet2s_"):
+        # small 2-level jet (coarse 192x96x96, fine cylinder of radius 12) for
+        # profiling the interface and boundary kernels
+        _, model, storage = args.variant.split("_")
+        flags, centre = synth.jet_two_level(24, 12, 12, radius=12.0)
+        ctx = lbm.lbm_create(model, storage, (24, 12, 12), False, flags, 1.0 / (3 * 8e-5 + 0.5),
+                             0.18 if model == "d3q19" else 0.0, stream.cuda_stream)
+        lbm.lbm_set_inflow(ctx, centre[0], centre[1], 8.0, 0.05, 0.01, 389)
+        lbm.lbm_step(ctx, W)
+        lbm.lbm_set_profiling(ctx, True)
+        lbm.lbm_step(ctx, K)
+        pms, pn = lbm.lbm_get_profile(ctx)
+        lbm.lbm_destroy(ctx)
+        if rank == 0:
+            print(json.dumps({"kernel_only": True, "variant": args.variant,
+                              "ms_per_coarse_step": {k: float(v) / K for k, v in
+                                                     zip(["update", "c2f", "f2c", "bc", "other"], pms)},
+                              "launches": [int(x) for x in pn]}), flush=True)
+        return
     if args.kernel_only:
         model, storage = args.variant.split("_")
         r = run_uniform(lbm, torch, model, storage, field, K, W, stream)
