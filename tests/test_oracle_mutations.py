@@ -1,0 +1,125 @@
+"""The oracle's pins catch plausible mistakes: each test plants one mistake in
+the oracle (monkeypatched, on the CPU) and checks that a pin of
+test_oracle_collision / test_oracle_physics / test_oracle_nested now fails."""
+import math
+
+import pytest
+import torch
+
+import oracle.collision as C
+import oracle.lattice as Lat
+import oracle.solver as S
+from tests import test_oracle_collision as TC
+from tests import test_oracle_lattice as TL
+from tests import test_oracle_nested as TN
+from tests import test_oracle_physics as TP
+
+
+def plant(monkeypatch, module, name, new):
+    """Replace an oracle function, also where a test module imported it by name."""
+    old = getattr(module, name)
+    monkeypatch.setattr(module, name, new)
+    for m in (TC, TL, TN, TP):
+        if getattr(m, name, None) is old:
+            monkeypatch.setattr(m, name, new)
+
+
+def fails(fn, *args):
+    try:
+        fn(*args)
+    except AssertionError:
+        return True
+    return False
+
+
+def test_wrong_sign_in_a_velocity_is_caught(monkeypatch):
+    bad = list(Lat._D3Q19[1])
+    bad[9] = -bad[9]                      # e_9 = (1, -1, 0) -> (1, 1, 0)
+    monkeypatch.setattr(Lat, "_D3Q19", (Lat._D3Q19[0], tuple(bad), Lat._D3Q19[2]))
+    assert fails(TL.test_velocity_set_shape, 19)
+
+
+def test_wrong_weight_is_caught(monkeypatch):
+    monkeypatch.setattr(Lat, "_W27", {0: 8 / 27, 1: 2 / 27, 2: 1 / 54, 3: 1 / 108})
+    assert fails(TL.test_weights_float_match_exact, 27)
+
+
+def test_dropped_quadratic_term_in_equilibrium_is_caught(monkeypatch):
+    orig = C.feq_incompressible
+
+    def feq(drho, u, Q=19):
+        e = Lat.velocities(Q).to(C.DTYPE)
+        w = Lat.weights(Q)
+        eu = e @ u
+        return w[:, None] * (drho[None] + 3.0 * eu - 1.5 * (u * u).sum(0)[None])
+    plant(monkeypatch, C, "feq_incompressible", feq)
+    assert fails(TP.test_shear_wave_viscosity, "d3q19", 1.2) or fails(TC.test_mrt_shear_projection_closed_form)
+
+
+def test_transposed_mrt_row_is_caught(monkeypatch):
+    orig = C.mrt_matrix
+
+    def M():
+        m = orig().clone()
+        m[[4, 9]] = m[[9, 4]]             # shear row mu12 swapped with the trace row
+        return m
+    plant(monkeypatch, C, "mrt_matrix", M)
+    assert fails(TC.test_mrt_shear_projection_closed_form)
+
+
+def test_wrong_smagorinsky_factor_is_caught(monkeypatch):
+    plant(monkeypatch, C, "tau_total",
+          lambda tau0, cs, Qn: tau0 + (torch.sqrt(tau0 * tau0 + 9.0 * cs * cs * Qn) - tau0) / 2.0)
+    assert fails(TC.test_smagorinsky_tau_solves_quadratic)
+
+
+def test_pre_collision_moments_in_cascade_are_caught(monkeypatch):
+    orig = C.fclb_relax
+
+    def relax(kappa, omega, rho, force=None):
+        out = orig(kappa, omega, rho, force)
+        k = kappa
+        out[:, C.IDX[(2, 2, 0)]] = k[:, C.IDX[(2, 0, 0)]] * k[:, C.IDX[(0, 2, 0)]]   # pre instead of post
+        return out
+    plant(monkeypatch, C, "fclb_relax", relax)
+    assert fails(TC.test_fclb_conserves_and_fixed_point) or fails(TP.test_shear_wave_viscosity, "d3q27", 1.8) \
+        or fails(TC.test_fclb_second_order_relaxation) or fails(TC.test_fclb_omega_one_gives_product_equilibrium)
+
+
+def test_transposed_central_moment_matrix_is_caught(monkeypatch):
+    orig = C.central_moment_matrix
+    plant(monkeypatch, C, "central_moment_matrix", lambda u: orig(u).transpose(1, 2).contiguous())
+    assert fails(TC.test_central_moments_match_table2_polynomials)
+
+
+def test_missing_interface_rescaling_is_caught(monkeypatch):
+    monkeypatch.setattr(S.NestedSolver, "_taus_cf", lambda self, l, S_c: (S_c * 0 + 2.0, S_c * 0 + 3.0))
+    assert fails(TN.test_shear_wave_stress_crosses_interfaces, "d3q19")
+
+
+def test_wrong_temporal_interpolation_is_caught(monkeypatch):
+    orig = S.NestedSolver._c2f
+
+    def c2f(self, l, s, old, new, oldS, newS):
+        return orig(self, l, 0, new, new, newS, newS)   # always the new coarse values
+    monkeypatch.setattr(S.NestedSolver, "_c2f", c2f)
+    assert fails(TN.test_shear_wave_across_refined_slab, "d3q19")
+
+
+def test_old_only_temporal_interpolation_is_caught(monkeypatch):
+    orig = S.NestedSolver._c2f
+
+    def c2f(self, l, s, old, new, oldS, newS):
+        return orig(self, l, 0, old, old, oldS, oldS)   # always the old coarse values
+    monkeypatch.setattr(S.NestedSolver, "_c2f", c2f)
+    assert fails(TN.test_shear_wave_across_refined_slab, "d3q19")
+
+
+def test_wrong_inflow_velocity_is_caught(monkeypatch):
+    orig = S.NestedSolver._apply_bc
+
+    def bc(self, l, sub):
+        self.inflow = dict(self.inflow, perturb=0.02)
+        return orig(self, l, sub)
+    monkeypatch.setattr(S.NestedSolver, "_apply_bc", bc)
+    assert fails(TN.test_inflow_ghosts_carry_disc_velocity, "d3q19")
