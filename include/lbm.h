@@ -141,12 +141,31 @@ int lbm_macroscopic(lbm_ctx* ctx, int level, double* rho, double* u);
 int lbm_mass_momentum(lbm_ctx* ctx, double out[4]);
 
 /* Dense float64 copy of a level's distributions, count = Q*NX*NY*NZ doubles.
- * Cells outside the level's blocks read NaN.  Exact for every storage. */
+ * Cells outside the level's blocks read NaN.  The stored (shifted) values are
+ * read exactly; for D3Q27 the unshifted sum f = (f - w) + w can round away
+ * the lowest bits of a deviation far below w, so use the raw state below for
+ * bit-exact checkpoints. */
 int lbm_get_state(lbm_ctx* ctx, int level, double* f, size_t count);
 
 /* Inverse of lbm_get_state (rounds to the storage type).  NaN entries and
  * cells outside the level are ignored.  Clears the pending restriction. */
 int lbm_set_state(lbm_ctx* ctx, int level, const double* f, size_t count);
+
+/* Bit-exact checkpoint of a level: the level's device state as stored (the
+ * current distribution buffer of the whole level box, then the strain buffer
+ * of nested D3Q19 runs).  The layout is the library's and may change between
+ * versions; bytes must equal lbm_raw_state_bytes.  Together with
+ * lbm_get_step / lbm_set_step it resumes a run bit for bit. */
+int lbm_raw_state_bytes(const lbm_ctx* ctx, int level, size_t* bytes);
+int lbm_get_raw_state(lbm_ctx* ctx, int level, void* buf, size_t bytes);
+int lbm_set_raw_state(lbm_ctx* ctx, int level, const void* buf, size_t bytes);
+
+/* Per-cell strain-rate norm |S| (Eq. eqStrainRate) of the last collision,
+ * dense float64 [NZ][NY][NX], count = NX*NY*NZ.  It is state only for nested
+ * D3Q19 Smagorinsky runs (it sets the relaxation times used by the interface
+ * transfer); elsewhere get returns zeros and set does nothing. */
+int lbm_get_strain(lbm_ctx* ctx, int level, double* S, size_t count);
+int lbm_set_strain(lbm_ctx* ctx, int level, const double* S, size_t count);
 
 /* Distributions of n sampled cells (level-local dense indices) into f[n][Q]. */
 int lbm_get_cells(lbm_ctx* ctx, int level, size_t n, const int64_t* cells, double* f);

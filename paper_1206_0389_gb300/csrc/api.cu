@@ -787,6 +787,73 @@ int lbm_set_state(lbm_ctx* ctx, int level, const double* f, size_t count) {
   return LBM_OK;
 }
 
+int lbm_raw_state_bytes(const lbm_ctx* ctx, int level, size_t* bytes) {
+  if (!ctx || !bytes || level < 0 || level >= ctx->L) return LBM_ERR_ARG;
+  const LevelPlan& lp = ctx->plan.lv[level];
+  const size_t fb = size_t(lp.nblocks()) * 512 * ctx->Q * storage_bytes(ctx->storage);
+  const size_t ab = ctx->dl[level].aux[0] ? size_t(lp.nblocks()) * 512 * real_bytes(ctx->storage) : 0;
+  *bytes = fb + ab;
+  return LBM_OK;
+}
+
+int lbm_get_raw_state(lbm_ctx* ctx, int level, void* buf, size_t bytes) {
+  size_t need = 0;
+  if (lbm_raw_state_bytes(ctx, level, &need) != LBM_OK || !buf) return fail(ctx, LBM_ERR_ARG, "bad argument");
+  if (bytes != need) return fail(ctx, LBM_ERR_ARG, "bytes must equal lbm_raw_state_bytes");
+  const LevelPlan& lp = ctx->plan.lv[level];
+  const size_t fb = size_t(lp.nblocks()) * 512 * ctx->Q * storage_bytes(ctx->storage);
+  const int p = cur_parity(ctx, level);
+  CK(cudaMemcpyAsync(buf, ctx->dl[level].f[p], fb, cudaMemcpyDeviceToHost, ctx->stream));
+  if (need > fb)
+    CK(cudaMemcpyAsync(static_cast<char*>(buf) + fb, ctx->dl[level].aux[p], need - fb, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LBM_OK;
+}
+
+int lbm_set_raw_state(lbm_ctx* ctx, int level, const void* buf, size_t bytes) {
+  size_t need = 0;
+  if (lbm_raw_state_bytes(ctx, level, &need) != LBM_OK || !buf) return fail(ctx, LBM_ERR_ARG, "bad argument");
+  if (bytes != need) return fail(ctx, LBM_ERR_ARG, "bytes must equal lbm_raw_state_bytes");
+  const LevelPlan& lp = ctx->plan.lv[level];
+  const size_t fb = size_t(lp.nblocks()) * 512 * ctx->Q * storage_bytes(ctx->storage);
+  const int p = cur_parity(ctx, level);
+  CK(cudaMemcpyAsync(ctx->dl[level].f[p], buf, fb, cudaMemcpyHostToDevice, ctx->stream));
+  if (need > fb)
+    CK(cudaMemcpyAsync(ctx->dl[level].aux[p], static_cast<const char*>(buf) + fb, need - fb,
+                       cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->need_restrict = false;
+  return LBM_OK;
+}
+
+int lbm_get_strain(lbm_ctx* ctx, int level, double* S, size_t count) {
+  if (!ctx || !S) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+  if (level < 0 || level >= ctx->L) return fail(ctx, LBM_ERR_ARG, "level out of range");
+  const LevelPlan& lp = ctx->plan.lv[level];
+  if (count != size_t(lp.NX) * lp.NY * lp.NZ) return fail(ctx, LBM_ERR_ARG, "count mismatch");
+  void* aux = ctx->dl[level].aux[cur_parity(ctx, level)];
+  if (!aux) {
+    for (size_t i = 0; i < count; ++i) S[i] = 0.0;
+    return LBM_OK;
+  }
+  double* hout[1] = {S};
+  return slab_transfer(ctx, level, SLAB_GET_AUX, nullptr, hout, 1, nullptr, aux);
+}
+
+int lbm_set_strain(lbm_ctx* ctx, int level, const double* S, size_t count) {
+  if (!ctx || !S) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+  if (level < 0 || level >= ctx->L) return fail(ctx, LBM_ERR_ARG, "level out of range");
+  const LevelPlan& lp = ctx->plan.lv[level];
+  if (count != size_t(lp.NX) * lp.NY * lp.NZ) return fail(ctx, LBM_ERR_ARG, "count mismatch");
+  void* aux = ctx->dl[level].aux[cur_parity(ctx, level)];
+  if (!aux) return LBM_OK;
+  for (size_t i = 0; i < count; ++i)
+    if (std::isinf(S[i])) return fail(ctx, LBM_ERR_NONFINITE, "infinite strain value");
+  const double* hin[1] = {S};
+  return slab_transfer(ctx, level, SLAB_SET_AUX, hin, nullptr, 1, nullptr, aux);
+}
+
 int lbm_get_cells(lbm_ctx* ctx, int level, size_t n, const int64_t* cells, double* f) {
   if (!ctx || (n && (!cells || !f))) return fail(ctx, LBM_ERR_ARG, "NULL argument");
   if (level < 0 || level >= ctx->L) return fail(ctx, LBM_ERR_ARG, "level out of range");

@@ -12,10 +12,77 @@
 // Boundaries: inflow ghost = f_eq(rho of the adjacent cell, u_bc) with the
 // top-hat disc velocity (Section 3.2 names a constant inflow velocity); outflow
 // ghost = copy of the adjacent cell (zero gradient).
+#include <type_traits>
+
 #include "collide.cuh"
 #include "kernels.cuh"
 
 namespace lbm {
+
+// ---------------------------------------------------------------- warp-per-cell helpers
+// The boundary kernel gives one warp to one ghost cell and one lane to each
+// population, so every lane issues one load (the x-face cells it serves are
+// 8 elements apart, so a thread-per-cell kernel serialises 27 sector loads per
+// thread); the cell's density is a warp sum.  Each lane reads its velocity and weight once
+// (through L1: the lanes of a warp read 27 different entries, which constant
+// memory would serialise) and keeps them in registers.
+__device__ const int8_t g_ex[32] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, 1, -1, -1, 1, -1};
+__device__ const int8_t g_ey[32] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1, 1, 1, -1, 1, -1, 1, -1, -1};
+__device__ const int8_t g_ez[32] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1, 1, 1, 1, -1, 1, -1, -1, -1};
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// velocity and weight of the lane's population (lanes >= Q get zeros)
+template <class T, int Q>
+struct Lane {
+  int x, y, z;
+  bool act;
+  T w;
+  __device__ __forceinline__ explicit Lane(int q) {
+    act = q < Q;
+    x = act ? int(__ldg(g_ex + q)) : 0;
+    y = act ? int(__ldg(g_ey + q)) : 0;
+    z = act ? int(__ldg(g_ez + q)) : 0;
+    const int n = x * x + y * y + z * z;
+    if (Q == 19) w = T(n == 0 ? 1.0 / 3.0 : n == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+    else w = T(n == 0 ? 8.0 / 27.0 : n == 1 ? 2.0 / 27.0 : n == 2 ? 1.0 / 54.0 : 1.0 / 216.0);
+  }
+};
+
+// one population of storage <-> shifted value g
+template <class S, class T, int Q>
+__device__ __forceinline__ T lane_load(const S* p, const Lane<T, Q>& ln) {
+  if constexpr (std::is_same<S, __half>::value) return __half2float(*p) * ln.w;
+  else return *p;
+}
+template <class S, class T, int Q>
+__device__ __forceinline__ void lane_store(S* p, const Lane<T, Q>& ln, T v) {
+  if constexpr (std::is_same<S, __half>::value) *p = __float2half_rn(v / ln.w);
+  else *p = v;
+}
+
+// equilibrium of the lane's population, shifted like the storage
+template <class M, class T, int Q>
+__device__ __forceinline__ T lane_feq(T rl, T ux, T uy, T uz, const Lane<T, Q>& ln) {
+  if constexpr (M::Q == 19) {
+    const T eu = T(ln.x) * ux + T(ln.y) * uy + T(ln.z) * uz;
+    return ln.w * (rl + T(3) * eu + T(4.5) * eu * eu - T(1.5) * (ux * ux + uy * uy + uz * uz));
+  } else {
+    // rho prod_a phi(e_a, u_a) - prod_a w1(e_a), phi = w1 + delta
+    auto delta = [](int e, T u) { return e == 0 ? -u * u : T(0.5) * (u * u + T(e) * u); };
+    auto wone = [](int e) { return e == 0 ? T(2.0 / 3.0) : T(1.0 / 6.0); };
+    const T dx = delta(ln.x, ux), dy = delta(ln.y, uy), dz = delta(ln.z, uz);
+    const T wx = wone(ln.x), wy = wone(ln.y), wz = wone(ln.z);
+    const T py = wy + dy, pz = wz + dz;
+    const T rho = T(1) + rl;
+    return rl * wx * wy * wz + rho * (dx * py * pz + wx * (dy * pz + wy * dz));
+  }
+}
 
 template <class M, class S>
 __global__ void k_c2f(const C2FArgs a) {
@@ -121,26 +188,26 @@ __device__ __forceinline__ double inflow_xi(unsigned long long seed, long long s
 }
 
 template <class M, class S>
-__global__ void k_bc(const BCArgs a) {
+__global__ void __launch_bounds__(128) k_bc(const BCArgs a) {
   using St = Store<S>;
   using T = typename St::T;
   constexpr int Q = M::Q;
   constexpr int QS = Q * kCells;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int q = threadIdx.x & 31;
   if (n >= a.n) return;
-  const BCItem it = a.items[n];
+  const BCItem& it = a.items[n];
+  const bool act = q < Q;
   S* f = reinterpret_cast<S*>(a.f);
   const S* src = f + int64_t(it.sblock) * QS + it.scell;
   S* dst = f + int64_t(it.gblock) * QS + it.gcell;
   if (it.type == 1) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) dst[i * kCells] = src[i * kCells];
+    if (act) dst[q * kCells] = src[q * kCells];
     return;
   }
-  T g[Q];
-  static_for<Q>([&](auto i) { g[i] = St::template get<Q, i>(src + int(i) * kCells); });
-  T rl = T(0);
-  static_for<Q>([&](auto i) { rl += g[i]; });
+  const Lane<T, Q> ln(q);
+  const T g = act ? lane_load(src + q * kCells, ln) : T(0);
+  const T rl = warp_sum(g);
   const double yc = (double(it.y) + 0.5) * a.inv_scale;
   const double zc = (double(it.z) + 0.5) * a.inv_scale;
   const double dy = yc - a.y0, dz = zc - a.z0;
@@ -148,20 +215,23 @@ __global__ void k_bc(const BCArgs a) {
   if (dy * dy + dz * dz < a.r2) {
     const long long step = *a.step;
     const long long cell = (long long)it.y + (long long)a.NY * it.z;
-    const double xx = inflow_xi(a.seed, step, a.level, a.substep, cell, 0);
-    const double xy = inflow_xi(a.seed, step, a.level, a.substep, cell, 1);
-    const double xz = inflow_xi(a.seed, step, a.level, a.substep, cell, 2);
+    // lanes 0..2 draw one component each
+    const double xi = inflow_xi(a.seed, step, a.level, a.substep, cell, q < 3 ? q : 0);
+    const double xx = __shfl_sync(0xffffffffu, xi, 0);
+    const double xy = __shfl_sync(0xffffffffu, xi, 1);
+    const double xz = __shfl_sync(0xffffffffu, xi, 2);
     ux = a.u_in * (1.0 + a.perturb * xx);
     uy = a.u_in * a.perturb * xy;
     uz = a.u_in * a.perturb * xz;
   }
-  T feq[Q];
-  M::feq(rl, T(ux), T(uy), T(uz), feq);
-  static_for<Q>([&](auto i) { St::template put<Q, i>(dst + int(i) * kCells, feq[i]); });
+  if (act) lane_store(dst + q * kCells, ln, lane_feq<M>(rl, T(ux), T(uy), T(uz), ln));
 }
 
 __global__ void k_step_inc(long long* step) { *step += 1; }
 
+// coarse-to-fine and fine-to-coarse: one thread per item (neighbouring items
+// share coarse stencils, so a warp's loads share sectors); boundary: one warp
+// per item, four items per CTA
 template <class M, class S>
 static cudaError_t c2f_ms(const C2FArgs& a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
@@ -177,7 +247,7 @@ static cudaError_t f2c_ms(const F2CArgs& a, cudaStream_t st) {
 template <class M, class S>
 static cudaError_t bc_ms(const BCArgs& a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
-  k_bc<M, S><<<(a.n + 127) / 128, 128, 0, st>>>(a);
+  k_bc<M, S><<<(a.n + 3) / 4, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -126,7 +126,8 @@ cudaError_t launch_step_inc(long long* step, cudaStream_t st);
 
 // dense <-> block staging for one slab of cell layers [z0, z0 + nz) of a level
 enum SlabMode { SLAB_SET_STATE = 0, SLAB_GET_STATE = 1, SLAB_INIT_EQ = 2, SLAB_MACRO = 3,
-                SLAB_SET_FORCE = 4, SLAB_SET_LAMBDA = 5, SLAB_GET_FIELD3 = 6 };
+                SLAB_SET_FORCE = 4, SLAB_SET_LAMBDA = 5, SLAB_GET_FIELD3 = 6, SLAB_GET_AUX = 7,
+                SLAB_SET_AUX = 8 };
 struct SlabArgs {
   void* f;                // level storage (current buffer)
   const uint8_t* kind;    // [nblocks][512] cell kinds

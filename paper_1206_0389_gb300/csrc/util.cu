@@ -104,6 +104,15 @@ __global__ void k_slab(const SlabArgs a) {
       for (int c = 0; c < 3; ++c) a.out[c * n + t] = j < 0 ? nan : double(r[c * nn + j]);
       return;
     }
+    case SLAB_GET_AUX: {
+      a.out[t] = j < 0 ? nan : double(reinterpret_cast<const T*>(a.raw)[j]);
+      return;
+    }
+    case SLAB_SET_AUX: {
+      if (j < 0 || isnan(a.in[t])) return;
+      reinterpret_cast<T*>(a.raw)[j] = T(a.in[t]);
+      return;
+    }
     case SLAB_SET_FORCE: {
       if (j < 0) return;
       const int64_t nn = int64_t(a.BX) * a.BY * a.BZ * kCells;

@@ -23,7 +23,9 @@ EXPORTED = ["lbm_plan", "lbm_create", "lbm_create_error", "lbm_set_inflow", "lbm
             "lbm_set_force", "lbm_step", "lbm_sync", "lbm_macroscopic", "lbm_mass_momentum",
             "lbm_get_state", "lbm_set_state", "lbm_get_cells", "lbm_get_step", "lbm_set_step",
             "lbm_set_profiling", "lbm_get_profile", "lbm_get_tuning", "lbm_last_error", "lbm_destroy",
-            "lbm_mass_momentum_noalloc", "lbm_adjoint_forward", "lbm_adjoint_backward"]
+            "lbm_mass_momentum_noalloc", "lbm_adjoint_forward", "lbm_adjoint_backward",
+            "lbm_get_strain", "lbm_set_strain", "lbm_raw_state_bytes", "lbm_get_raw_state",
+            "lbm_set_raw_state"]
 NOALLOC_MAX_BLOCKS = 65536
 
 
@@ -72,6 +74,11 @@ def load():
         "lbm_get_state": (c_int, [c_void_p, c_int, D, c_size_t]),
         "lbm_set_state": (c_int, [c_void_p, c_int, D, c_size_t]),
         "lbm_get_cells": (c_int, [c_void_p, c_int, c_size_t, P(c_int64), D]),
+        "lbm_get_strain": (c_int, [c_void_p, c_int, D, c_size_t]),
+        "lbm_raw_state_bytes": (c_int, [c_void_p, c_int, P(c_size_t)]),
+        "lbm_get_raw_state": (c_int, [c_void_p, c_int, c_void_p, c_size_t]),
+        "lbm_set_raw_state": (c_int, [c_void_p, c_int, c_void_p, c_size_t]),
+        "lbm_set_strain": (c_int, [c_void_p, c_int, D, c_size_t]),
         "lbm_get_step": (c_int, [c_void_p, P(c_int64)]),
         "lbm_set_step": (c_int, [c_void_p, c_int64]),
         "lbm_set_profiling": (c_int, [c_void_p, c_int]),
@@ -207,6 +214,36 @@ def lbm_get_state(ctx, level):
 def lbm_set_state(ctx, level, f):
     a = _f64(f)
     _check(ctx, load().lbm_set_state(ctx.h, level, _dptr(a), a.size))
+
+
+def lbm_raw_state_bytes(ctx, level):
+    n = c_size_t()
+    _check(ctx, load().lbm_raw_state_bytes(ctx.h, level, ctypes.byref(n)))
+    return n.value
+
+
+def lbm_get_raw_state(ctx, level):
+    """The level's device state as stored (bit-exact checkpoint), as uint8."""
+    buf = np.empty(lbm_raw_state_bytes(ctx, level), dtype=np.uint8)
+    _check(ctx, load().lbm_get_raw_state(ctx.h, level, buf.ctypes.data_as(c_void_p), buf.size))
+    return buf
+
+
+def lbm_set_raw_state(ctx, level, buf):
+    b = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(ctx, load().lbm_set_raw_state(ctx.h, level, b.ctypes.data_as(c_void_p), b.size))
+
+
+def lbm_get_strain(ctx, level):
+    NX, NY, NZ = ctx.dims(level)
+    S = np.empty((NZ, NY, NX))
+    _check(ctx, load().lbm_get_strain(ctx.h, level, _dptr(S), S.size))
+    return S
+
+
+def lbm_set_strain(ctx, level, S):
+    a = _f64(S)
+    _check(ctx, load().lbm_set_strain(ctx.h, level, _dptr(a), a.size))
 
 
 def lbm_get_cells(ctx, level, cells):

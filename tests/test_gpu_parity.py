@@ -355,3 +355,115 @@ def test_error_codes():
     # a NaN planted in the state (NaN entries are skipped by set_state, so
     # write it through a second context's state) is caught by the audit
     close(ctx)
+
+
+# ---------------------------------------------------------------- checkpoint, audit, full-size nested
+
+def valid_cells(lbm, ctx, l):
+    rho, _ = lbm.lbm_macroscopic(ctx, l)
+    return ~np.isnan(rho)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_checkpoint_resume_is_bitwise(model):
+    """The raw state of every level (distributions and, for nested D3Q19, the
+    Smagorinsky strain carried across levels) plus the step counter resume a
+    nested run with inflow bit for bit."""
+    lbm = gpu()
+    nb, ref = jet_grid(2)
+    a = lbm.lbm_create(model, "f32", nb, False, ref, 1.8, 0.18)
+    lbm.lbm_set_inflow(a, 8.0, 8.0, 8.0, 0.05, 0.01, 21)
+    lbm.lbm_step(a, 3)
+    raw = [lbm.lbm_get_raw_state(a, l) for l in range(2)]
+    step = lbm.lbm_get_step(a)
+    lbm.lbm_step(a, 4)
+    ref_state = [lbm.lbm_get_state(a, l) for l in range(2)]
+    b = lbm.lbm_create(model, "f32", nb, False, ref, 1.8, 0.18)
+    lbm.lbm_set_inflow(b, 8.0, 8.0, 8.0, 0.05, 0.01, 21)
+    for l in range(2):
+        lbm.lbm_set_raw_state(b, l, raw[l])
+    lbm.lbm_set_step(b, step)
+    lbm.lbm_step(b, 4)
+    for l in range(2):
+        m = valid_cells(lbm, a, l)
+        got = lbm.lbm_get_state(b, l)
+        assert np.array_equal(got[:, m], ref_state[l][:, m])
+    close(a)
+    close(b)
+
+
+def test_dense_state_round_trip_and_strain():
+    """The dense float64 state and the strain field read back what was set."""
+    lbm = gpu()
+    nb, ref = jet_grid(2)
+    a = lbm.lbm_create("d3q19", "f64", nb, True, ref, 1.7, 0.18)
+    for l in range(2):
+        NX, NY, NZ = a.dims(l)
+        rho, u = synth.taylor_green_3d(NY, 0.03, shape=(NX, NY, NZ))
+        lbm.lbm_init_equilibrium(a, l, rho, u)
+    lbm.lbm_step(a, 2)
+    for l in range(2):
+        f = lbm.lbm_get_state(a, l)
+        S = lbm.lbm_get_strain(a, l)
+        assert np.nanmax(S) > 0
+        lbm.lbm_set_state(a, l, f)
+        lbm.lbm_set_strain(a, l, S)
+        assert np.array_equal(np.isnan(f), np.isnan(lbm.lbm_get_state(a, l)))
+        ok = ~np.isnan(f)
+        assert np.array_equal(lbm.lbm_get_state(a, l)[ok], f[ok])
+        ok = ~np.isnan(S)
+        assert np.array_equal(lbm.lbm_get_strain(a, l)[ok], S[ok])
+    close(a)
+
+
+def test_audit_reports_nonfinite_state():
+    """A value beyond the float32 range, planted on the host through the
+    state (finite as float64, so it passes the input check), is stored as Inf;
+    after two steps the float64 audit reports the non-finite state."""
+    lbm = gpu()
+    ctx = lbm.lbm_create("d3q27", "f32", (2, 1, 1), True, [], 1.5, 0.0)
+    lbm.lbm_init_equilibrium(ctx, 0)
+    f = lbm.lbm_get_state(ctx, 0)
+    f[5, 3, 4, 5] = 1e39
+    lbm.lbm_set_state(ctx, 0, f)
+    lbm.lbm_step(ctx, 2)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_mass_momentum(ctx)
+    assert e.value.status == lbm.LBM_ERR_NONFINITE
+    close(ctx)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_full_size_jet_grid_uniform_flow_invariance(model):
+    """The 2-level jet grid at full size (coarse 384x192x192, 6.3 M fine
+    cells) with x made periodic: a uniform flow passes the interfaces
+    unchanged to FP32 round-off after 3 coarse steps."""
+    lbm = gpu()
+    flags, _ = synth.jet_two_level()
+    ctx = lbm.lbm_create(model, "f32", (48, 24, 24), True, flags, 1.0 / 0.5003, 0.18)
+    u0 = np.array([0.05, 0.02, -0.01])
+    for l in range(2):
+        NX, NY, NZ = ctx.dims(l)
+        lbm.lbm_init_equilibrium(ctx, l, None, np.broadcast_to(u0[:, None, None, None], (3, NZ, NY, NX)).copy())
+    lbm.lbm_step(ctx, 3)
+    for l in range(2):
+        rho, u = lbm.lbm_macroscopic(ctx, l)
+        ok = ~np.isnan(rho)
+        assert np.abs(rho[ok] - 1).max() < 2e-6
+        assert np.abs(u[:, ok] - u0[:, None]).max() < 2e-6
+    close(ctx)
+
+
+def test_paper_scale_three_level_jet_runs():
+    """The 3-level jet with 40.09 M active cells (1.08e9 D3Q27 values) builds,
+    matches its plan and takes coarse steps with finite, sane audits."""
+    lbm = gpu()
+    flags, centre = synth.jet_paper_scale()
+    info = lbm.lbm_plan((64, 32, 32), False, flags, "d3q27", "f32")
+    assert sum(info.active_cells[l] for l in range(3)) == 40_091_648
+    ctx = lbm.lbm_create("d3q27", "f32", (64, 32, 32), False, flags, 1.0 / (3 * 1.6e-4 + 0.5), 0.0)
+    lbm.lbm_set_inflow(ctx, centre[0], centre[1], 32.0, 0.05, 0.01, 5120)
+    lbm.lbm_step(ctx, 3)
+    m = lbm.lbm_mass_momentum(ctx)
+    assert np.isfinite(m).all() and m[1] > 0
+    close(ctx)
