@@ -365,14 +365,25 @@ def ours(args):
     field = synth.spectrum_field(N_GRID, seed=1206 + rank)
     K, W = args.steps, args.warmup
 
-    if args.kernel_only and args.variant.startswith("jet2s_"):
-        # small 2-level jet (coarse 192x96x96, fine cylinder of radius 12) for
-        # profiling the interface and boundary kernels
-        _, model, storage = args.variant.split("_")
-        flags, centre = synth.jet_two_level(24, 12, 12, radius=12.0)
-        ctx = lbm.lbm_create(model, storage, (24, 12, 12), False, flags, 1.0 / (3 * 8e-5 + 0.5),
+    if args.kernel_only and args.variant.startswith(("jet2s_", "jet3s_", "jet3p_")):
+        # jets for profiling the interface and boundary kernels:
+        # jet2s = 2 levels (coarse 192x96x96, fine cylinder of radius 12);
+        # jet3s = the 3-level jet at half the paper's scale (coarse
+        # 256x128x128, D = 16, 1.8 GB in FP32); jet3p = the paper-scale
+        # 3-level jet (11.3 GB in FP32: launch lists only, no full captures)
+        kind, model, storage = args.variant.split("_")
+        if kind == "jet2s":
+            nb, D = (24, 12, 12), 8.0
+            flags, centre = synth.jet_two_level(*nb, radius=12.0)
+        elif kind == "jet3p":
+            nb, D = (64, 32, 32), 32.0
+            flags, centre = synth.jet_paper_scale()
+        else:
+            nb, D = (32, 16, 16), 16.0
+            flags, centre = synth.jet_three_level(*nb, r1=(4.0, 16.0), r2=(6.0, 12.0), x1=(0, 96), x2=(0, 48))
+        ctx = lbm.lbm_create(model, storage, nb, False, flags, 1.0 / (3 * 8e-5 + 0.5),
                              0.18 if model == "d3q19" else 0.0, stream.cuda_stream)
-        lbm.lbm_set_inflow(ctx, centre[0], centre[1], 8.0, 0.05, 0.01, 389)
+        lbm.lbm_set_inflow(ctx, centre[0], centre[1], D, 0.05, 0.01, 389)
         lbm.lbm_step(ctx, W)
         lbm.lbm_set_profiling(ctx, True)
         lbm.lbm_step(ctx, K)

@@ -82,7 +82,7 @@ typedef struct {
   int64_t updated_cells[LBM_MAX_LEVELS]; /* active + hidden layer 1                 */
   int64_t hidden_cells[LBM_MAX_LEVELS];  /* hidden layers 1 and 2                   */
   int64_t ghost_cells[LBM_MAX_LEVELS];   /* coarse-to-fine ghost cells              */
-  int64_t bc_cells[LBM_MAX_LEVELS];      /* inflow/outflow ghost cells              */
+  int64_t bc_cells[LBM_MAX_LEVELS];      /* inflow ghost cells (x = -1)             */
   int64_t updates_per_coarse_step;       /* sum_l updated_cells[l] * 2^l            */
   int64_t active_updates_per_coarse_step;/* sum_l active_cells[l] * 2^l             */
   int64_t device_bytes;                  /* device memory lbm_create would allocate */
@@ -155,7 +155,10 @@ int lbm_set_state(lbm_ctx* ctx, int level, const double* f, size_t count);
  * current distribution buffer of the whole level box, then the strain buffer
  * of nested D3Q19 runs).  The layout is the library's and may change between
  * versions; bytes must equal lbm_raw_state_bytes.  Together with
- * lbm_get_step / lbm_set_step it resumes a run bit for bit. */
+ * lbm_get_step / lbm_set_step it resumes a run bit for bit when the resumed
+ * context runs the same stream-collide variant (lbm_get_tuning of the saved
+ * context, passed as LBM_LAUNCH_SHAPE): variants compiled for another
+ * register cap may round a few operations differently. */
 int lbm_raw_state_bytes(const lbm_ctx* ctx, int level, size_t* bytes);
 int lbm_get_raw_state(lbm_ctx* ctx, int level, void* buf, size_t bytes);
 int lbm_set_raw_state(lbm_ctx* ctx, int level, const void* buf, size_t bytes);
@@ -202,7 +205,12 @@ int lbm_get_profile(lbm_ctx* ctx, double ms[5], int64_t launches[5]);
 
 /* Launch configuration of the stream-collide kernel chosen by the autotuner:
  * threads per CTA, the minimum resident CTAs per SM the kernel was compiled
- * for (1 = no register cap), and CTAs per launch (0 = one CTA per block). */
+ * for (1 = no register cap), and CTAs per launch (0 = one CTA per block).
+ * lbm_create times the shapes (128,1) (256,1) (128,8) (256,4), each
+ * with one CTA per block and as a persistent grid, on the largest update
+ * launch of the schedule.  Environment: LBM_AUTOTUNE=0 skips the timing and
+ * keeps (256,1, one CTA per block); LBM_LAUNCH_SHAPE="threads,min,persistent"
+ * fixes one listed shape (lbm_create fails with LBM_ERR_ARG otherwise). */
 int lbm_get_tuning(const lbm_ctx* ctx, int* threads, int* min_ctas_per_sm, int* ctas);
 
 /* Mass/momentum audit for callers that cannot let the library allocate

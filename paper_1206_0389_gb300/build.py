@@ -29,6 +29,7 @@ def _compile(src):
     if src.endswith(".cu"):
         cmd = [nvcc(), "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC",
                "-Xptxas", "-v", "-c", path, "-o", obj]
+
     else:
         cmd = [nvcc(), "-std=c++17", "-O2", "-x", "c++", "-Xcompiler", "-fPIC", "-c", path, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)

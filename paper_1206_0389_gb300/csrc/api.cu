@@ -31,8 +31,6 @@ thread_local std::string g_create_error;
 
 struct Op {
   enum Kind { UPDATE, C2F, F2C, BC, INC } kind;
-  int level = 0;   // UPDATE: lowest level of the group; others: level concerned
-  int s = 0;       // C2F substep; BC substep index
   UpdateArgs ua{};
   C2FArgs ca{};
   F2CArgs fa{};
@@ -44,6 +42,8 @@ struct DevLevel {
   void* aux[2] = {nullptr, nullptr};
   uint8_t* kind = nullptr;
   C2FItem* c2f = nullptr;
+  C2FChunk* c2f_chunks = nullptr;
+  C2FCell* c2f_cells = nullptr;
   F2CItem* f2c = nullptr;
   BCItem* bc = nullptr;
   double* force = nullptr;
@@ -129,6 +129,8 @@ void free_all(lbm_ctx* c) {
     cudaFree(d.aux[1]);
     cudaFree(d.kind);
     cudaFree(d.c2f);
+    cudaFree(d.c2f_chunks);
+    cudaFree(d.c2f_cells);
     cudaFree(d.f2c);
     cudaFree(d.bc);
     cudaFree(d.force);
@@ -165,58 +167,67 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
         break;
       }
     auto sub = [&](int l) { return k / (1 << (L - 1 - l)); };
-    for (int l = std::max(lmin, 1); l < L; ++l) {
-      const int s = sub(l) % 2;
-      const LevelPlan& fp = c->plan.lv[l];
-      const LevelPlan& cp = c->plan.lv[l - 1];
+    // coarse-to-fine for every level starting a substep: one launch (level
+    // l writes its ghost cells and reads active / hidden-1 cells of l-1)
+    if (std::max(lmin, 1) < L) {
       Op op;
       op.kind = Op::C2F;
-      op.level = l;
-      op.s = s;
       C2FArgs& a = op.ca;
-      a.items = c->dl[l].c2f;
-      a.n = int(fp.c2f.size());
-      const int pc = par[l - 1];
-      a.c_old = c->dl[l - 1].f[s == 0 ? pc : 1 - pc];
-      a.c_new = c->dl[l - 1].f[pc];
-      a.a_old = les ? c->dl[l - 1].aux[s == 0 ? pc : 1 - pc] : nullptr;
-      a.a_new = les ? c->dl[l - 1].aux[pc] : nullptr;
-      a.f_dst = c->dl[l].f[par[l]];
-      a.fa_dst = les ? c->dl[l].aux[par[l]] : nullptr;
-      a.s = s;
-      a.tau0_c = cp.tau0;
-      a.tau0_f = fp.tau0;
       a.cs2_3 = cs2_3;
-      ops.push_back(op);
+      for (int l = std::max(lmin, 1); l < L; ++l) {
+        const int s = sub(l) % 2;
+        const LevelPlan& fp = c->plan.lv[l];
+        const LevelPlan& cp = c->plan.lv[l - 1];
+        if (fp.c2f_chunks.empty()) continue;
+        C2FLevel& v = a.lv[a.nlv++];
+        v.chunks = c->dl[l].c2f_chunks;
+        v.items = c->dl[l].c2f;
+        v.cells = c->dl[l].c2f_cells;
+        v.n = int(fp.c2f_chunks.size());
+        const int pc = par[l - 1];
+        v.c_old = c->dl[l - 1].f[s == 0 ? pc : 1 - pc];
+        v.c_new = c->dl[l - 1].f[pc];
+        v.a_old = les ? c->dl[l - 1].aux[s == 0 ? pc : 1 - pc] : nullptr;
+        v.a_new = les ? c->dl[l - 1].aux[pc] : nullptr;
+        v.f_dst = c->dl[l].f[par[l]];
+        v.fa_dst = les ? c->dl[l].aux[par[l]] : nullptr;
+        v.s = s;
+        v.tau0_c = cp.tau0;
+        v.tau0_f = fp.tau0;
+        a.n += v.n;
+      }
+      if (a.n > 0) ops.push_back(op);
     }
+    // inflow / outflow ghosts of the same levels (after the interface: an
+    // inflow ghost may take its density from a coarse-to-fine ghost cell)
     if (!c->plan.periodic_x) {
+      Op op;
+      op.kind = Op::BC;
+      BCArgs& b = op.ba;
+      b.step = c->d_step;
+      b.y0 = c->y0;
+      b.z0 = c->z0;
+      b.r2 = (0.5 * c->diameter) * (0.5 * c->diameter);
+      b.u_in = c->u_in;
+      b.perturb = c->perturb;
+      b.seed = c->seed;
       for (int l = lmin; l < L; ++l) {
         const LevelPlan& lp = c->plan.lv[l];
-        Op op;
-        op.kind = Op::BC;
-        op.level = l;
-        op.s = sub(l);
-        BCArgs& b = op.ba;
-        b.items = c->dl[l].bc;
-        b.n = int(lp.bc.size());
-        b.f = c->dl[l].f[par[l]];
-        b.level = l;
-        b.substep = sub(l);
-        b.NY = lp.NY;
-        b.step = c->d_step;
-        b.y0 = c->y0;
-        b.z0 = c->z0;
-        b.r2 = (0.5 * c->diameter) * (0.5 * c->diameter);
-        b.u_in = c->u_in;
-        b.perturb = c->perturb;
-        b.inv_scale = std::ldexp(1.0, -l);
-        b.seed = c->seed;
-        ops.push_back(op);
+        if (lp.bc.empty()) continue;
+        BCLevel& v = b.lv[b.nlv++];
+        v.items = c->dl[l].bc;
+        v.n = int(lp.bc.size());
+        v.f = c->dl[l].f[par[l]];
+        v.level = l;
+        v.substep = sub(l);
+        v.NY = lp.NY;
+        v.inv_scale = std::ldexp(1.0, -l);
+        b.n += v.n;
       }
+      if (b.n > 0) ops.push_back(op);
     }
     Op up;
     up.kind = Op::UPDATE;
-    up.level = lmin;
     UpdateArgs& u = up.ua;
     for (int l = 0; l < L; ++l) {
       const LevelPlan& lp = c->plan.lv[l];
@@ -235,24 +246,31 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
     u.force = c->has_force ? c->dl[0].force : nullptr;
     ops.push_back(up);
     for (int l = lmin; l < L; ++l) par[l] ^= 1;
-    for (int l = L - 1; l >= std::max(lmin, 1); --l) {
-      if (sub(l) % 2 != 1) continue;
-      const LevelPlan& fp = c->plan.lv[l];
-      const LevelPlan& cp = c->plan.lv[l - 1];
+    // fine-to-coarse after the second substep of each fine level: one launch
+    // (level l-1's hidden cells take level l's active cells, which no other
+    // level of the launch writes)
+    {
       Op op;
       op.kind = Op::F2C;
-      op.level = l;
       F2CArgs& a = op.fa;
-      a.items = c->dl[l - 1].f2c;
-      a.n = int(cp.f2c.size());
-      a.f_src = c->dl[l].f[par[l]];
-      a.fa_src = les ? c->dl[l].aux[par[l]] : nullptr;
-      a.c_dst = c->dl[l - 1].f[par[l - 1]];
-      a.ca_dst = les ? c->dl[l - 1].aux[par[l - 1]] : nullptr;
-      a.tau0_c = cp.tau0;
-      a.tau0_f = fp.tau0;
       a.cs2_3 = cs2_3;
-      ops.push_back(op);
+      for (int l = L - 1; l >= std::max(lmin, 1); --l) {
+        if (sub(l) % 2 != 1) continue;
+        const LevelPlan& fp = c->plan.lv[l];
+        const LevelPlan& cp = c->plan.lv[l - 1];
+        if (cp.f2c.empty()) continue;
+        F2CLevel& v = a.lv[a.nlv++];
+        v.items = c->dl[l - 1].f2c;
+        v.n = int(cp.f2c.size());
+        v.f_src = c->dl[l].f[par[l]];
+        v.fa_src = les ? c->dl[l].aux[par[l]] : nullptr;
+        v.c_dst = c->dl[l - 1].f[par[l - 1]];
+        v.ca_dst = les ? c->dl[l - 1].aux[par[l - 1]] : nullptr;
+        v.tau0_c = cp.tau0;
+        v.tau0_f = fp.tau0;
+        a.n += v.n;
+      }
+      if (a.n > 0) ops.push_back(op);
     }
   }
   Op inc;
@@ -288,15 +306,17 @@ int restrict_all(lbm_ctx* ctx) {
   const bool les = ctx->model == LBM_D3Q19_MRT_LES;
   for (int l = ctx->L - 1; l >= 1; --l) {
     F2CArgs a{};
-    a.items = ctx->dl[l - 1].f2c;
-    a.n = int(ctx->plan.lv[l - 1].f2c.size());
-    a.f_src = ctx->dl[l].f[0];
-    a.fa_src = les ? ctx->dl[l].aux[0] : nullptr;
+    F2CLevel& v = a.lv[0];
+    a.nlv = 1;
+    v.items = ctx->dl[l - 1].f2c;
+    v.n = a.n = int(ctx->plan.lv[l - 1].f2c.size());
+    v.f_src = ctx->dl[l].f[0];
+    v.fa_src = les ? ctx->dl[l].aux[0] : nullptr;
     const int pc = l - 1 == 0 ? ctx->parity0 : 0;
-    a.c_dst = ctx->dl[l - 1].f[pc];
-    a.ca_dst = les ? ctx->dl[l - 1].aux[pc] : nullptr;
-    a.tau0_c = ctx->plan.lv[l - 1].tau0;
-    a.tau0_f = ctx->plan.lv[l].tau0;
+    v.c_dst = ctx->dl[l - 1].f[pc];
+    v.ca_dst = les ? ctx->dl[l - 1].aux[pc] : nullptr;
+    v.tau0_c = ctx->plan.lv[l - 1].tau0;
+    v.tau0_f = ctx->plan.lv[l].tau0;
     a.cs2_3 = 3.0 * ctx->cs * ctx->cs;
     CK(launch_f2c(ctx->model, ctx->storage, a, ctx->stream));
   }
@@ -333,7 +353,7 @@ int build_graphs(lbm_ctx* ctx) {
 }
 
 // Pick the stream-collide launch shape by timing the largest update launch of
-// the schedule: threads per CTA in {128, 256, 512}, one CTA per block or a
+// the schedule: threads per CTA in {128, 256}, one CTA per block or a
 // persistent grid of (CTAs per SM x SMs).  Writes only the other buffer.
 int autotune(lbm_ctx* ctx) {
   const char* env = std::getenv("LBM_AUTOTUNE");
@@ -348,7 +368,26 @@ int autotune(lbm_ctx* ctx) {
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   int bt = 256, bm = 1, bc = 0;
-  const int shapes[5][2] = {{128, 1}, {256, 1}, {512, 1}, {128, 8}, {256, 4}};
+  // (no 512-thread shape: with one pass over the 512 cells of a block its
+  // kernel is optimised into differently rounded arithmetic)
+  const int shapes[4][2] = {{128, 1}, {256, 1}, {128, 8}, {256, 4}};
+  // LBM_LAUNCH_SHAPE="threads,min_ctas_per_sm,persistent" fixes one of the
+  // shapes below without timing (profilers distort the timings).
+  if (const char* fixed = std::getenv("LBM_LAUNCH_SHAPE")) {
+    int t = 0, mb = 0, pers = -1;
+    bool ok = std::sscanf(fixed, "%d,%d,%d", &t, &mb, &pers) == 3 && (pers == 0 || pers == 1);
+    bool listed = false;
+    for (const auto& sh : shapes) listed |= sh[0] == t && sh[1] == mb;
+    int occ = 0;
+    ok = ok && listed && update_occupancy(ctx->model, ctx->storage, t, mb, &occ) == cudaSuccess && occ >= 1;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!ok) return fail(ctx, LBM_ERR_ARG, std::string("LBM_LAUNCH_SHAPE not a listed shape: ") + fixed);
+    ctx->threads = t;
+    ctx->minb = mb;
+    ctx->ctas = pers ? occ * ctx->sms : 0;
+    return LBM_OK;
+  }
   for (const auto& sh : shapes) {
     const int t = sh[0], mb = sh[1];
     int occ = 0;
@@ -560,6 +599,8 @@ int lbm_create(lbm_ctx** out, lbm_model model, lbm_storage storage, const lbm_gr
       }
     }
     if ((ce = upload(&d.kind, lp.kind)) != cudaSuccess || (ce = upload(&d.c2f, lp.c2f)) != cudaSuccess ||
+        (ce = upload(&d.c2f_chunks, lp.c2f_chunks)) != cudaSuccess ||
+        (ce = upload(&d.c2f_cells, lp.c2f_cells)) != cudaSuccess ||
         (ce = upload(&d.f2c, lp.f2c)) != cudaSuccess || (ce = upload(&d.bc, lp.bc)) != cudaSuccess)
       return bail(LBM_ERR_OOM, std::string("plan tables: ") + cudaGetErrorString(ce));
     const int16_t moff = int16_t(masks.size() / 16);
@@ -589,7 +630,7 @@ int lbm_create(lbm_ctx** out, lbm_model model, lbm_storage storage, const lbm_gr
   ctx->need_restrict = ctx->L > 1;
   ce = cudaStreamSynchronize(ctx->stream);
   if (ce != cudaSuccess) return bail(LBM_ERR_CUDA, std::string("init: ") + cudaGetErrorString(ce));
-  if (autotune(ctx) != LBM_OK) return bail(LBM_ERR_CUDA, "autotune: " + ctx->err);
+  if (int rc = autotune(ctx); rc != LBM_OK) return bail(rc, "autotune: " + ctx->err);
   // the tuning runs wrote the second buffers; clear them again
   for (int l = 0; l < ctx->L; ++l) {
     const size_t fb = size_t(ctx->plan.lv[l].nblocks()) * 512 * ctx->Q * sb;

@@ -9,9 +9,14 @@
 // Fine-to-coarse: hidden coarse cells take the mean over their 8 children of
 // f_eq + r_fc (f~ - f_eq), r_fc = 2 (tau_c - 1) / (tau_f - 1), with tau_f the
 // child's own and tau_c = tau0_c + 3 Cs^2 (2 |S|_child).
-// Boundaries: inflow ghost = f_eq(rho of the adjacent cell, u_bc) with the
-// top-hat disc velocity (Section 3.2 names a constant inflow velocity); outflow
-// ghost = copy of the adjacent cell (zero gradient).
+// Inflow: ghost = f_eq(rho of the adjacent cell, u_bc) with the top-hat disc
+// velocity (Section 3.2 names a constant inflow velocity).  The zero-gradient
+// outflow (ghost = copy of the adjacent cell) has no kernel here: the
+// stream-collide kernel pulls those populations from the adjacent cell.
+// Streaming only pulls, so a ghost cell is read only through the populations
+// that point from it into an updated cell; the kernels write just those (the
+// planner's per-item mask; e_x = +1 at the inflow) and leave the others as
+// they were.
 #include <type_traits>
 
 #include "collide.cuh"
@@ -84,87 +89,170 @@ __device__ __forceinline__ T lane_feq(T rl, T ux, T uy, T uz, const Lane<T, Q>& 
   }
 }
 
+// Fine-to-coarse: four lanes serve one item; lane r loads the child pair
+// p = r (one aligned two-element load per population), the partial sums meet
+// by two xor shuffles, and lane r stores the populations i with i % 4 == r.
+constexpr int kLanes = 4;
+
+// the level that owns global item g of a multi-level launch (a register
+// copy: the unrolled selects keep the launch parameters in the constant
+// bank); g becomes the level-local index
+template <class Lv, class Args>
+__device__ __forceinline__ Lv pick_level(const Args& a, int& g) {
+  Lv L = a.lv[0];
+#pragma unroll
+  for (int k = 1; k < kMaxL; ++k)
+    if (k < a.nlv && g >= L.n) {
+      g -= L.n;
+      L = a.lv[k];
+    }
+  return L;
+}
+
+template <class T>
+__device__ __forceinline__ T quad_sum(T v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  return v;
+}
+
+// One CTA per chunk (kC2FMaxItems threads): stage the chunk's distinct
+// coarse stencil cells in shared memory (for substep 1 already averaged over
+// t and t+1), population by population so that consecutive threads read
+// consecutive cells; then one thread per ghost cell interpolates from shared
+// memory.  The distinct cells of a chunk number about a quarter of its
+// 8 x items stencil references, and every global read is a coalesced run.
 template <class M, class S>
-__global__ void k_c2f(const C2FArgs a) {
+__global__ void __launch_bounds__(kC2FMaxItems) k_c2f(const C2FArgs a) {
   using St = Store<S>;
   using T = typename St::T;
   constexpr int Q = M::Q;
   constexpr int QS = Q * kCells;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= a.n) return;
-  const C2FItem it = a.items[n];
+  constexpr int MC = c2f_max_cells(std::is_same<S, double>::value ? LBM_F64 : LBM_F32);
+  __shared__ T sv[Q * MC];
+  __shared__ T sS[MC];
+  int g = blockIdx.x;
+  const C2FLevel L = pick_level<C2FLevel>(a, g);
+  const C2FChunk ch = L.chunks[g];
+  const int nc = ch.ncells;
+  const S* co = reinterpret_cast<const S*>(L.c_old);
+  const S* cn = reinterpret_cast<const S*>(L.c_new);
+  // each thread stages whole cells (MC / blockDim of them at most), all Q
+  // loads of a cell issued before the first is used
+#pragma unroll 1
+  for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+    const C2FCell cl = L.cells[ch.first_cell + j];
+    const int64_t o = int64_t(cl.cblock) * QS + cl.ccell;
+    T v[Q];
+    static_for<Q>([&](auto i) { v[i] = St::template get<Q, i>(co + o + int(i) * kCells); });
+    if (L.s == 1) {
+      static_for<Q>([&](auto i) { v[i] = T(0.5) * (v[i] + St::template get<Q, i>(cn + o + int(i) * kCells)); });
+    }
+    static_for<Q>([&](auto i) { sv[int(i) * MC + j] = v[i]; });
+    if (L.a_old != nullptr) {
+      const int64_t jj = int64_t(cl.cblock) * kCells + cl.ccell;
+      T sj = reinterpret_cast<const T*>(L.a_old)[jj];
+      if (L.s == 1) sj = T(0.5) * (sj + reinterpret_cast<const T*>(L.a_new)[jj]);
+      sS[j] = sj;
+    }
+  }
+  __syncthreads();
+  if (int(threadIdx.x) >= ch.nitems) return;
+  const C2FItem it = L.items[ch.first_item + threadIdx.x];
   const T tx = (it.tbits & 1) ? T(0.75) : T(0.25);
   const T ty = (it.tbits & 2) ? T(0.75) : T(0.25);
   const T tz = (it.tbits & 4) ? T(0.75) : T(0.25);
   T F[Q];
   static_for<Q>([&](auto i) { F[i] = T(0); });
   T Sh = T(0);
-  const S* co = reinterpret_cast<const S*>(a.c_old);
-  const S* cn = reinterpret_cast<const S*>(a.c_new);
-#pragma unroll 2
+#pragma unroll
   for (int k = 0; k < 8; ++k) {
-    const T wx = (k & 1) ? tx : T(1) - tx;
-    const T wy = (k & 2) ? ty : T(1) - ty;
-    const T wz = (k & 4) ? tz : T(1) - tz;
-    const T W = wz * wy * wx;
-    const int64_t base = int64_t(it.cblock[k]) * QS + it.ccell[k];
-    static_for<Q>([&](auto i) {
-      T v = St::template get<Q, i>(co + base + int(i) * kCells);
-      if (a.s == 1) v = T(0.5) * (v + St::template get<Q, i>(cn + base + int(i) * kCells));
-      F[i] += W * v;
-    });
-    if (a.a_old != nullptr) {
-      const int64_t j = int64_t(it.cblock[k]) * kCells + it.ccell[k];
-      T sv = reinterpret_cast<const T*>(a.a_old)[j];
-      if (a.s == 1) sv = T(0.5) * (sv + reinterpret_cast<const T*>(a.a_new)[j]);
-      Sh += W * sv;
-    }
+    const T W = ((k & 4) ? tz : T(1) - tz) * ((k & 2) ? ty : T(1) - ty) * ((k & 1) ? tx : T(1) - tx);
+    const int sl = it.slot[k];
+    static_for<Q>([&](auto i) { F[i] += W * sv[int(i) * MC + sl]; });
+    if (L.a_old != nullptr) Sh += W * sS[sl];
   }
   T rl, ux, uy, uz;
   M::moments(F, rl, ux, uy, uz);
   T feq[Q];
   M::feq(rl, ux, uy, uz, feq);
-  const T tc = T(a.tau0_c) + T(a.cs2_3) * Sh;
-  const T tf = T(a.tau0_f) + T(a.cs2_3) * Sh / T(2);
-  const T r = (tf - T(1)) / (T(2) * (tc - T(1)));
-  S* fd = reinterpret_cast<S*>(a.f_dst) + int64_t(it.fblock) * QS + it.fcell;
-  static_for<Q>([&](auto i) { St::template put<Q, i>(fd + int(i) * kCells, feq[i] + r * (F[i] - feq[i])); });
-  if (a.fa_dst != nullptr) reinterpret_cast<T*>(a.fa_dst)[int64_t(it.fblock) * kCells + it.fcell] = Sh / T(2);
+  const T tc = T(L.tau0_c) + T(a.cs2_3) * Sh;
+  const T tf = T(L.tau0_f) + T(a.cs2_3) * Sh / T(2);
+  const T rr = (tf - T(1)) / (T(2) * (tc - T(1)));
+  S* fd = reinterpret_cast<S*>(L.f_dst) + int64_t(it.fblock) * QS + it.fcell;
+  static_for<Q>([&](auto i) {
+    if ((it.need >> int(i)) & 1u) St::template put<Q, i>(fd + int(i) * kCells, feq[i] + rr * (F[i] - feq[i]));
+  });
+  if (L.fa_dst != nullptr) reinterpret_cast<T*>(L.fa_dst)[int64_t(it.fblock) * kCells + it.fcell] = Sh / T(2);
+}
+
+// two adjacent stored values starting at an even index: one aligned load
+template <class S, int Q, int i>
+__device__ __forceinline__ void get_pair(const S* p, typename Store<S>::T& a, typename Store<S>::T& b) {
+  if constexpr (std::is_same<S, double>::value) {
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    a = v.x;
+    b = v.y;
+  } else if constexpr (std::is_same<S, float>::value) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    a = v.x;
+    b = v.y;
+  } else {
+    const __half2 v = __ldg(reinterpret_cast<const __half2*>(p));
+    a = __low2float(v) * float(Lattice<Q>::w(i));
+    b = __high2float(v) * float(Lattice<Q>::w(i));
+  }
 }
 
 template <class M, class S>
-__global__ void k_f2c(const F2CArgs a) {
+__global__ void __launch_bounds__(128) k_f2c(const F2CArgs a) {
   using St = Store<S>;
   using T = typename St::T;
   constexpr int Q = M::Q;
   constexpr int QS = Q * kCells;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= a.n) return;
-  const F2CItem it = a.items[n];
-  const S* fs = reinterpret_cast<const S*>(a.f_src);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = t & (kLanes - 1);
+  const bool valid = (t / kLanes) < a.n;
+  int g = valid ? t / kLanes : a.n - 1;
+  const F2CLevel L = pick_level<F2CLevel>(a, g);
+  const F2CItem& it = L.items[g];
+  const int64_t base = int64_t(it.fblock[r]) * QS + it.fcell[r];
+  const S* fs = reinterpret_cast<const S*>(L.f_src);
   T acc[Q];
   static_for<Q>([&](auto i) { acc[i] = T(0); });
   T accS = T(0);
-#pragma unroll 2
-  for (int ch = 0; ch < 8; ++ch) {
-    const int64_t base = int64_t(it.fblock[ch]) * QS + it.fcell[ch];
-    T g[Q];
-    static_for<Q>([&](auto i) { g[i] = St::template get<Q, i>(fs + base + int(i) * kCells); });
-    T Sk = T(0);
-    if (a.fa_src != nullptr) Sk = reinterpret_cast<const T*>(a.fa_src)[int64_t(it.fblock[ch]) * kCells + it.fcell[ch]];
+  // add f_eq + r_fc (f - f_eq) of one child
+  auto child = [&](const T (&g)[Q], T Sk) {
     T rl, ux, uy, uz;
     M::moments(g, rl, ux, uy, uz);
     T feq[Q];
     M::feq(rl, ux, uy, uz, feq);
-    const T tf = T(a.tau0_f) + T(a.cs2_3) * Sk;
-    const T tc = T(a.tau0_c) + T(a.cs2_3) * T(2) * Sk;
-    const T r = T(2) * (tc - T(1)) / (tf - T(1));
-    static_for<Q>([&](auto i) { acc[i] += feq[i] + r * (g[i] - feq[i]); });
+    const T tf = T(L.tau0_f) + T(a.cs2_3) * Sk;
+    const T tc = T(L.tau0_c) + T(a.cs2_3) * T(2) * Sk;
+    const T rr = T(2) * (tc - T(1)) / (tf - T(1));
+    static_for<Q>([&](auto i) { acc[i] += feq[i] + rr * (g[i] - feq[i]); });
     accS += T(2) * Sk;
+  };
+  {
+    T g0[Q], g1[Q];
+    static_for<Q>([&](auto i) { get_pair<S, Q, i>(fs + base + int(i) * kCells, g0[i], g1[i]); });
+    T S0 = T(0), S1 = T(0);
+    if (L.fa_src != nullptr) {
+      const T* fa = reinterpret_cast<const T*>(L.fa_src) + int64_t(it.fblock[r]) * kCells + it.fcell[r];
+      S0 = fa[0];
+      S1 = fa[1];
+    }
+    child(g0, S0);
+    child(g1, S1);
   }
-  S* cd = reinterpret_cast<S*>(a.c_dst) + int64_t(it.cblock) * QS + it.ccell;
-  static_for<Q>([&](auto i) { St::template put<Q, i>(cd + int(i) * kCells, acc[i] / T(8)); });
-  if (a.ca_dst != nullptr) reinterpret_cast<T*>(a.ca_dst)[int64_t(it.cblock) * kCells + it.ccell] = accS / T(8);
+  static_for<Q>([&](auto i) { acc[i] = quad_sum(acc[i]); });
+  accS = quad_sum(accS);
+  if (!valid) return;
+  S* cd = reinterpret_cast<S*>(L.c_dst) + int64_t(it.cblock) * QS + it.ccell;
+  static_for<Q>([&](auto i) {
+    if ((int(i) & (kLanes - 1)) == r) St::template put<Q, i>(cd + int(i) * kCells, acc[i] / T(8));
+  });
+  if (L.ca_dst != nullptr && r == 0) reinterpret_cast<T*>(L.ca_dst)[int64_t(it.cblock) * kCells + it.ccell] = accS / T(8);
 }
 
 // SplitMix64 (Steele, Lea & Flood 2014): advance by the golden gamma, then mix.
@@ -193,30 +281,27 @@ __global__ void __launch_bounds__(128) k_bc(const BCArgs a) {
   using T = typename St::T;
   constexpr int Q = M::Q;
   constexpr int QS = Q * kCells;
-  const int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int q = threadIdx.x & 31;
   if (n >= a.n) return;
-  const BCItem& it = a.items[n];
+  const BCLevel L = pick_level<BCLevel>(a, n);
+  const BCItem& it = L.items[n];
   const bool act = q < Q;
-  S* f = reinterpret_cast<S*>(a.f);
+  S* f = reinterpret_cast<S*>(L.f);
   const S* src = f + int64_t(it.sblock) * QS + it.scell;
   S* dst = f + int64_t(it.gblock) * QS + it.gcell;
-  if (it.type == 1) {
-    if (act) dst[q * kCells] = src[q * kCells];
-    return;
-  }
   const Lane<T, Q> ln(q);
   const T g = act ? lane_load(src + q * kCells, ln) : T(0);
   const T rl = warp_sum(g);
-  const double yc = (double(it.y) + 0.5) * a.inv_scale;
-  const double zc = (double(it.z) + 0.5) * a.inv_scale;
+  const double yc = (double(it.y) + 0.5) * L.inv_scale;
+  const double zc = (double(it.z) + 0.5) * L.inv_scale;
   const double dy = yc - a.y0, dz = zc - a.z0;
   double ux = 0.0, uy = 0.0, uz = 0.0;
   if (dy * dy + dz * dz < a.r2) {
     const long long step = *a.step;
-    const long long cell = (long long)it.y + (long long)a.NY * it.z;
+    const long long cell = (long long)it.y + (long long)L.NY * it.z;
     // lanes 0..2 draw one component each
-    const double xi = inflow_xi(a.seed, step, a.level, a.substep, cell, q < 3 ? q : 0);
+    const double xi = inflow_xi(a.seed, step, L.level, L.substep, cell, q < 3 ? q : 0);
     const double xx = __shfl_sync(0xffffffffu, xi, 0);
     const double xy = __shfl_sync(0xffffffffu, xi, 1);
     const double xz = __shfl_sync(0xffffffffu, xi, 2);
@@ -224,24 +309,23 @@ __global__ void __launch_bounds__(128) k_bc(const BCArgs a) {
     uy = a.u_in * a.perturb * xy;
     uz = a.u_in * a.perturb * xz;
   }
-  if (act) lane_store(dst + q * kCells, ln, lane_feq<M>(rl, T(ux), T(uy), T(uz), ln));
+  if (act && ln.x == 1) lane_store(dst + q * kCells, ln, lane_feq<M>(rl, T(ux), T(uy), T(uz), ln));
 }
 
 __global__ void k_step_inc(long long* step) { *step += 1; }
 
-// coarse-to-fine and fine-to-coarse: one thread per item (neighbouring items
-// share coarse stencils, so a warp's loads share sectors); boundary: one warp
-// per item, four items per CTA
+// coarse-to-fine: one CTA per chunk; fine-to-coarse: four lanes per item, 32
+// items per CTA; boundary: one warp per item, four items per CTA
 template <class M, class S>
 static cudaError_t c2f_ms(const C2FArgs& a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
-  k_c2f<M, S><<<(a.n + 127) / 128, 128, 0, st>>>(a);
+  k_c2f<M, S><<<a.n, kC2FMaxItems, 0, st>>>(a);
   return cudaGetLastError();
 }
 template <class M, class S>
 static cudaError_t f2c_ms(const F2CArgs& a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
-  k_f2c<M, S><<<(a.n + 127) / 128, 128, 0, st>>>(a);
+  k_f2c<M, S><<<(a.n + 31) / 32, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 template <class M, class S>

@@ -14,7 +14,9 @@ constexpr int kMaxL = LBM_MAX_LEVELS;
 
 // one unit of stream-collide work: a block of one level, optionally masked.
 // edges: bit 2a (2a+1) set when the block sits on the low (high) face of a
-// level box that wraps periodically along axis a (x, y, z).
+// level box that wraps periodically along axis a (x, y, z); bit 6 set when
+// its +x face is the zero-gradient outflow x = NX (the populations entering
+// through it are pulled from the cell x = NX - 1 itself).
 struct WorkItem {
   int32_t block;
   uint8_t level;
@@ -50,30 +52,53 @@ struct UpdateArgs {
   const double* force;    // level 0 body force [3][nblocks*512] (block order) or nullptr
 };
 
-// coarse-to-fine: one fine ghost cell and its 8 coarse stencil cells
+// coarse-to-fine work comes in chunks of consecutive ghost cells (sorted by
+// their coarse stencil); a chunk lists its distinct coarse stencil cells once
+// (sorted by address), one CTA stages their values in shared memory, and the
+// items index that list
+struct C2FChunk {
+  int32_t first_item;
+  int32_t first_cell;
+  int16_t nitems;
+  int16_t ncells;
+};
+struct C2FCell {
+  int32_t cblock;
+  int16_t ccell;
+  int16_t pad;
+};
 struct C2FItem {
   int32_t fblock;
   int16_t fcell;
-  uint8_t tbits;  // bit a: weight of the upper coarse index along axis a is 3/4 (else 1/4)
+  uint8_t tbits;      // bit a: weight of the upper coarse index along axis a is 3/4 (else 1/4)
   uint8_t pad;
-  int32_t cblock[8];  // order (dz, dy, dx) with dx fastest; 0 = lower, 1 = upper index
-  int16_t ccell[8];
+  uint32_t need;      // bit i: population i is pulled by an updated cell of the level
+  uint16_t slot[8];   // stencil cells (dz, dy, dx order, dx fastest; 0 = lower,
+                      // 1 = upper index) as indices into the chunk's cell list
 };
+// chunk limits (distinct cells x Q values of the compute type stay at 27 KB
+// of shared memory)
+__host__ __device__ constexpr int c2f_max_cells(int storage) { return storage == LBM_F64 ? 128 : 256; }
+constexpr int kC2FMaxItems = 128;  // = threads per CTA
 
-// fine-to-coarse: one hidden coarse cell and its 8 children (dz, dy, dx order)
+// fine-to-coarse: one hidden coarse cell and its 8 children as 4 x-pairs
+// (pair p = dy + 2 dz): the children (2X, ...) at fcell[p] and (2X+1, ...) at
+// fcell[p] + 1 of block fblock[p]; fcell[p] is even, so a pair is one aligned
+// two-element load
 struct F2CItem {
   int32_t cblock;
   int16_t ccell;
   int16_t pad;
-  int32_t fblock[8];
-  int16_t fcell[8];
+  int32_t fblock[4];
+  int16_t fcell[4];
 };
 
 // boundary ghost cell
 struct BCItem {
   int32_t gblock;
   int16_t gcell;
-  int8_t type;  // 0 inflow (x = -1), 1 outflow (x = NX)
+  int8_t type;  // 0 inflow (x = -1); only the populations pulled into the
+                // domain (e_x = +1) are written
   int8_t pad;
   int32_t sblock;
   int16_t scell;
@@ -81,36 +106,59 @@ struct BCItem {
   int32_t y, z;  // level-local cell coordinates of the face cell
 };
 
-struct C2FArgs {
+// The interface and boundary launches each cover every level that needs the
+// transfer at that point of the schedule (they touch disjoint cells); level
+// j of a launch owns items [sum_{k<j} n_k, sum_{k<=j} n_k).
+struct C2FLevel {
+  const C2FChunk* chunks;
   const C2FItem* items;
-  int n;
+  const C2FCell* cells;
+  int n;              // chunks
+  int s;              // fine substep 0 or 1
   const void* c_old;  // coarse storage at t
   const void* c_new;  // coarse storage at t+1 (used when s == 1)
   const void* a_old;  // coarse |S| at t (LES) or nullptr
   const void* a_new;
   void* f_dst;        // fine storage receiving the ghost values
   void* fa_dst;       // fine |S| (LES) or nullptr
-  int s;              // fine substep 0 or 1
-  double tau0_c, tau0_f, cs2_3;  // cs2_3 = 3 Cs^2
+  double tau0_c, tau0_f;
+};
+struct C2FArgs {
+  C2FLevel lv[kMaxL];
+  int nlv;
+  int n;           // chunks of all levels
+  double cs2_3;    // 3 Cs^2
 };
 
-struct F2CArgs {
+struct F2CLevel {
   const F2CItem* items;
   int n;
   const void* f_src;  // fine storage at t+1
   const void* fa_src;
   void* c_dst;        // coarse storage at t+1
   void* ca_dst;
-  double tau0_c, tau0_f, cs2_3;
+  double tau0_c, tau0_f;
+};
+struct F2CArgs {
+  F2CLevel lv[kMaxL];
+  int nlv;
+  int n;
+  double cs2_3;
 };
 
-struct BCArgs {
+struct BCLevel {
   const BCItem* items;
   int n;
   void* f;  // level storage at the current time (ghosts written in place)
   int level, substep, NY;
+  double inv_scale;  // 2^-level
+};
+struct BCArgs {
+  BCLevel lv[kMaxL];
+  int nlv;
+  int n;
   const long long* step;  // device coarse-step counter
-  double y0, z0, r2, u_in, perturb, inv_scale;  // inv_scale = 2^-level
+  double y0, z0, r2, u_in, perturb;
   unsigned long long seed;
 };
 

@@ -12,6 +12,8 @@
 //            receive the coarse-to-fine transfer before every substep.
 #include "plan.h"
 
+#include "lattice.cuh"
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -252,7 +254,8 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
           w.level = uint8_t(l);
           w.edges = uint8_t((lp.wrap[0] && X == 0 ? 1 : 0) | (lp.wrap[0] && X == lp.BX - 1 ? 2 : 0) |
                             (lp.wrap[1] && Y == 0 ? 4 : 0) | (lp.wrap[1] && Y == lp.BY - 1 ? 8 : 0) |
-                            (lp.wrap[2] && Z == 0 ? 16 : 0) | (lp.wrap[2] && Z == lp.BZ - 1 ? 32 : 0));
+                            (lp.wrap[2] && Z == 0 ? 16 : 0) | (lp.wrap[2] && Z == lp.BZ - 1 ? 32 : 0) |
+                            (!px && bx == d.nbx - 1 ? 64 : 0));
           if (!d.refined[i]) {
             std::fill(k, k + 512, uint8_t(K_ACTIVE));
             lp.active_cells += 512;
@@ -306,49 +309,51 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
             }
           }
         }
-    // boundary ghost columns
+    // inflow ghost column x = -1 (the outflow needs none: the stream-collide
+    // kernel reads its zero-gradient ghosts from x = NX - 1, edges bit 6)
     if (!px) {
-      for (int side = 0; side < 2; ++side) {
-        const std::vector<uint8_t>& col = side == 0 ? bcl : bch;
-        const int gbx = side == 0 ? -1 : d.nbx;
-        const int sbx = side == 0 ? 0 : d.nbx - 1;
-        const int gx = side == 0 ? 7 : 0, sx = side == 0 ? 0 : 7;
-        for (int bz = 0; bz < d.nbz; ++bz)
-          for (int by = 0; by < d.nby; ++by) {
-            if (!col[by + int64_t(d.nby) * bz]) continue;
-            const int32_t gb = lp.box_id(gbx, by, bz);
-            const int32_t sb = lp.box_id(sbx, by, bz);
-            if (gb < 0) return "internal: boundary block outside its box";
-            if (sb < 0) continue;
-            for (int cz = 0; cz < 8; ++cz)
-              for (int cy = 0; cy < 8; ++cy) {
-                const int sc = sx + 8 * cy + 64 * cz;
-                const uint8_t sk = lp.kind[int64_t(sb) * 512 + sc];
-                if (sk == K_NONE) continue;
-                const int gc = gx + 8 * cy + 64 * cz;
-                lp.kind[int64_t(gb) * 512 + gc] = K_BC;
-                lp.bc_cells++;
-                BCItem it{};
-                it.gblock = gb;
-                it.gcell = int16_t(gc);
-                it.type = int8_t(side);
-                it.sblock = sb;
-                it.scell = int16_t(sc);
-                it.y = 8 * by + cy;
-                it.z = 8 * bz + cz;
-                lp.bc.push_back(it);
-              }
-          }
-      }
+      for (int bz = 0; bz < d.nbz; ++bz)
+        for (int by = 0; by < d.nby; ++by) {
+          if (!bcl[by + int64_t(d.nby) * bz]) continue;
+          const int32_t gb = lp.box_id(-1, by, bz);
+          const int32_t sb = lp.box_id(0, by, bz);
+          if (gb < 0) return "internal: boundary block outside its box";
+          if (sb < 0) continue;
+          for (int cz = 0; cz < 8; ++cz)
+            for (int cy = 0; cy < 8; ++cy) {
+              const int sc = 8 * cy + 64 * cz;
+              if (lp.kind[int64_t(sb) * 512 + sc] == K_NONE) continue;
+              const int gc = 7 + 8 * cy + 64 * cz;
+              lp.kind[int64_t(gb) * 512 + gc] = K_BC;
+              lp.bc_cells++;
+              BCItem it{};
+              it.gblock = gb;
+              it.gcell = int16_t(gc);
+              it.type = 0;
+              it.sblock = sb;
+              it.scell = int16_t(sc);
+              it.y = 8 * by + cy;
+              it.z = 8 * bz + cz;
+              lp.bc.push_back(it);
+            }
+        }
     }
     (void)box_of;
   }
 
   // ---------------------------------------------------------------- interface lists
+  // a ghost cell with its full stencil, before chunking
+  struct Ghost {
+    C2FItem it;
+    int32_t cblock[8];
+    int16_t ccell[8];
+  };
+  const int max_cells = c2f_max_cells(storage);
   for (int l = 1; l < L; ++l) {
     LevelPlan& f = P.lv[l];
     const LevelPlan& c = P.lv[l - 1];
     const DomainLevel& dc = D[l - 1];
+    std::vector<Ghost> ghosts;
     for (int bz = f.oz; bz < f.oz + f.BZ; ++bz)
       for (int by = f.oy; by < f.oy + f.BY; ++by)
         for (int bx = f.ox; bx < f.ox + f.BX; ++bx) {
@@ -375,10 +380,23 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
               lo[a] = i0;
               hi[a] = i1;
             }
-            C2FItem it{};
+            Ghost gh{};
+            C2FItem& it = gh.it;
             it.fblock = b;
             it.fcell = int16_t(cc);
             it.tbits = tb;
+            // populations some updated fine cell pulls from this ghost cell;
+            // all of them where an inflow/outflow ghost is taken from it
+            if (!px && (X == 0 || X == f.NX - 1)) it.need = (1u << P.Q) - 1u;
+            for (int i = 0; i < P.Q; ++i) {
+              int nx = X + ex27(i), ny = wrapi(Y + ey27(i), f.NY), nz = wrapi(Z + ez27(i), f.NZ);
+              if (px) nx = wrapi(nx, f.NX);
+              if (nx < 0 || nx >= f.NX) continue;
+              const int32_t nbk = f.box_id(nx >> 3, ny >> 3, nz >> 3);
+              if (nbk < 0) continue;
+              const uint8_t nk = f.kind[int64_t(nbk) * 512 + (nx & 7) + 8 * (ny & 7) + 64 * (nz & 7)];
+              if (nk == K_ACTIVE || nk == K_HIDDEN1) it.need |= 1u << i;
+            }
             for (int k = 0; k < 8; ++k) {
               const int ix = (k & 1) ? hi[0] : lo[0];
               const int iy = (k & 2) ? hi[1] : lo[1];
@@ -389,18 +407,55 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
               const uint8_t ck = c.kind[int64_t(cb) * 512 + ccell];
               if (ck != K_ACTIVE && ck != K_HIDDEN1)
                 return "interpolation stencil leaves the updated coarse cells (grid too tight)";
-              it.cblock[k] = cb;
-              it.ccell[k] = int16_t(ccell);
+              gh.cblock[k] = cb;
+              gh.ccell[k] = int16_t(ccell);
             }
-            f.c2f.push_back(it);
+            ghosts.push_back(gh);
           }
         }
     (void)dc;
-    // fine ghost cells that share a coarse stencil become neighbouring threads
-    std::stable_sort(f.c2f.begin(), f.c2f.end(), [](const C2FItem& a, const C2FItem& b) {
+    // fine ghost cells that share coarse stencils become neighbours, then
+    // consecutive ghosts form chunks of at most kC2FMaxItems items and
+    // max_cells distinct stencil cells
+    std::stable_sort(ghosts.begin(), ghosts.end(), [](const Ghost& a, const Ghost& b) {
       if (a.cblock[0] != b.cblock[0]) return a.cblock[0] < b.cblock[0];
       return a.ccell[0] < b.ccell[0];
     });
+    auto key = [](int32_t cb, int16_t cc) { return int64_t(cb) * 512 + cc; };
+    size_t g0 = 0;
+    while (g0 < ghosts.size()) {
+      std::vector<int64_t> cells;
+      size_t g1 = g0;
+      while (g1 < ghosts.size() && g1 - g0 < size_t(kC2FMaxItems)) {
+        int64_t add[8];
+        int na = 0;
+        for (int k = 0; k < 8; ++k) {
+          const int64_t kk = key(ghosts[g1].cblock[k], ghosts[g1].ccell[k]);
+          if (!std::binary_search(cells.begin(), cells.end(), kk) && std::find(add, add + na, kk) == add + na)
+            add[na++] = kk;
+        }
+        if (int(cells.size()) + na > max_cells) break;
+        for (int k = 0; k < na; ++k) cells.insert(std::upper_bound(cells.begin(), cells.end(), add[k]), add[k]);
+        ++g1;
+      }
+      C2FChunk ch{};
+      ch.first_item = int32_t(f.c2f.size());
+      ch.first_cell = int32_t(f.c2f_cells.size());
+      ch.nitems = int16_t(g1 - g0);
+      ch.ncells = int16_t(cells.size());
+      for (int64_t k : cells) f.c2f_cells.push_back(C2FCell{int32_t(k / 512), int16_t(k % 512), 0});
+      for (size_t g = g0; g < g1; ++g) {
+        C2FItem it = ghosts[g].it;
+        for (int k = 0; k < 8; ++k) {
+          const int64_t kk = key(ghosts[g].cblock[k], ghosts[g].ccell[k]);
+          it.slot[k] = uint16_t(std::lower_bound(cells.begin(), cells.end(), kk) - cells.begin());
+        }
+        f.c2f.push_back(it);
+      }
+      f.c2f_chunks.push_back(ch);
+      g0 = g1;
+    }
+    if (f.c2f_cells.size() >= (size_t(1) << 31)) return "too many coarse-to-fine cells";
   }
   for (int l = 0; l + 1 < L; ++l) {
     LevelPlan& c = P.lv[l];
@@ -422,8 +477,9 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
               const int fc = (x & 7) + 8 * (y & 7) + 64 * (z & 7);
               if (fb < 0 || f.kind[int64_t(fb) * 512 + fc] != K_ACTIVE)
                 return "internal: restriction child is not an active fine cell";
-              it.fblock[ch] = fb;
-              it.fcell[ch] = int16_t(fc);
+              if (ch & 1) continue;  // the odd child is fcell + 1 of the same block (x = 2X is even)
+              it.fblock[ch >> 1] = fb;
+              it.fcell[ch >> 1] = int16_t(fc);
             }
             c.f2c.push_back(it);
           }
@@ -440,7 +496,8 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
     if (aux) bytes += 2 * lp.nblocks() * 512 * int64_t(rb);
     bytes += lp.nblocks() * 512;  // kinds
     bytes += int64_t(lp.items.size() * sizeof(WorkItem) + lp.masks.size() * 4 +
-                     lp.c2f.size() * sizeof(C2FItem) + lp.f2c.size() * sizeof(F2CItem) +
+                     lp.c2f.size() * sizeof(C2FItem) + lp.c2f_chunks.size() * sizeof(C2FChunk) +
+                     lp.c2f_cells.size() * sizeof(C2FCell) + lp.f2c.size() * sizeof(F2CItem) +
                      lp.bc.size() * sizeof(BCItem));
   }
   P.device_bytes = bytes;

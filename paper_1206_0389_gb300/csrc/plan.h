@@ -27,7 +27,9 @@ struct LevelPlan {
   std::vector<uint8_t> kind;        // [nblocks][512] CellKind
   std::vector<WorkItem> items;      // stream-collide work of this level
   std::vector<uint32_t> masks;      // 16 words per masked item
-  std::vector<C2FItem> c2f;         // ghost cells of this level (l >= 1)
+  std::vector<C2FItem> c2f;         // ghost cells of this level (l >= 1), in chunks
+  std::vector<C2FChunk> c2f_chunks;
+  std::vector<C2FCell> c2f_cells;   // distinct coarse stencil cells per chunk
   std::vector<F2CItem> f2c;         // hidden cells of this level (l < L-1)
   std::vector<BCItem> bc;           // boundary ghost cells
   std::vector<int32_t> block_of;    // [nbz][nby][nbx] in-domain block -> box id or -1

@@ -12,7 +12,9 @@
 // extra element offset for leaving the block along -x is Xm (non-zero only
 // for cells with x == 0), along +x Xp (x == 7), likewise Ym/Yp/Zm/Zp, so the
 // source of population i is own_block + i*512 + cell - (e_x + 8 e_y + 64 e_z)
-// + X(e_x) + Y(e_y) + Z(e_z) with X(+1) = Xm, X(-1) = Xp, X(0) = 0.
+// + X(e_x) + Y(e_y) + Z(e_z) with X(+1) = Xm, X(-1) = Xp, X(0) = 0.  On the
+// zero-gradient outflow face (Xp = -1 for x == 7) the ghost copy of cell
+// (NX - 1, y', z') is read from that cell directly.
 #pragma once
 #include <algorithm>
 
@@ -49,7 +51,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
       }
       const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
       const int Xm = (x == 0) ? dxm * QS + 8 : 0;
-      const int Xp = (x == 7) ? dxp * QS - 8 : 0;
+      const int Xp = (x == 7) ? ((w.edges & 64) ? -1 : dxp * QS - 8) : 0;
       const int Ym = (y == 0) ? dym * QS + 64 : 0;
       const int Yp = (y == 7) ? dyp * QS - 64 : 0;
       const int Zm = (z == 0) ? dzm * QS + 512 : 0;
@@ -95,7 +97,6 @@ cudaError_t launch_ms(const UpdateArgs& a, int threads, int minb, int ctas, cuda
   const int grid = ctas > 0 ? std::min(ctas, a.nitems) : a.nitems;
   if (threads == 128 && minb == 1) k_update<M, S, 128, 1><<<grid, 128, 0, st>>>(a);
   else if (threads == 256 && minb == 1) k_update<M, S, 256, 1><<<grid, 256, 0, st>>>(a);
-  else if (threads == 512 && minb == 1) k_update<M, S, 512, 1><<<grid, 512, 0, st>>>(a);
   else if (threads == 128 && minb == 8) k_update<M, S, 128, 8><<<grid, 128, 0, st>>>(a);
   else if (threads == 256 && minb == 4) k_update<M, S, 256, 4><<<grid, 256, 0, st>>>(a);
   else return cudaErrorInvalidValue;
@@ -106,7 +107,6 @@ template <class M, class S>
 cudaError_t occ_ms(int threads, int minb, int* n) {
   if (threads == 128 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 1>, 128, 0);
   if (threads == 256 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 256, 1>, 256, 0);
-  if (threads == 512 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 512, 1>, 512, 0);
   if (threads == 128 && minb == 8) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 8>, 128, 0);
   if (threads == 256 && minb == 4) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 256, 4>, 256, 0);
   return cudaErrorInvalidValue;

@@ -223,6 +223,26 @@ def test_nested_parity_f64(model, levels, periodic_x):
 
 
 @pytest.mark.parametrize("model", MODELS)
+def test_nested_parity_refined_patch_on_inflow_face(model):
+    """A refined patch that touches the inflow face only in part: fine ghost
+    cells lie on x = 0, so fine inflow ghosts take their density from
+    coarse-to-fine ghost cells, and the disc straddles the patch edge."""
+    lbm = gpu()
+    nb = (4, 3, 3)
+    r = np.zeros((3, 3, 4), dtype=bool)
+    r[1, 1, 0:2] = True
+    ctx, orc = make_pair(model, "f64", nb, False, [r], omega=1.7, cs=0.18)
+    init_both(ctx, orc, nested_fields(orc))
+    lbm.lbm_set_inflow(ctx, 12.0, 12.0, 12.0, 0.05, 0.01, 77)
+    orc.set_inflow(12.0, 12.0, 12.0, 0.05, 0.01, 77)
+    lbm.lbm_step(ctx, 3)
+    orc.step(3)
+    d, s = compare_levels(ctx, orc)
+    assert d <= 1e-12, d
+    close(ctx)
+
+
+@pytest.mark.parametrize("model", MODELS)
 def test_nested_parity_f32_per_step(model):
     lbm = gpu()
     nb, ref = jet_grid(2)
@@ -364,14 +384,64 @@ def valid_cells(lbm, ctx, l):
     return ~np.isnan(rho)
 
 
+# launch shapes grouped by compiled kernel variant (threads per CTA and the
+# register cap of min CTAs per SM): within a group only the thread count and
+# the grid differ
+SHAPE_GROUPS = [["128,1,0", "256,1,0", "128,1,1", "256,1,1"],
+                ["128,8,0", "128,8,1"], ["256,4,0", "256,4,1"]]
+
+
+def run_with_shape(lbm, monkeypatch, sh, model, storage, steps=4):
+    monkeypatch.setenv("LBM_LAUNCH_SHAPE", sh)
+    nb, ref = jet_grid(2)
+    ctx = lbm.lbm_create(model, storage, nb, False, ref, 1.8, 0.18)
+    t, m, c = lbm.lbm_get_tuning(ctx)
+    assert (t, m, c > 0) == tuple(int(v) for v in sh.split(",")[:2]) + (sh.endswith(",1"),)
+    lbm.lbm_set_inflow(ctx, 8.0, 8.0, 8.0, 0.05, 0.01, 21)
+    for l in range(2):
+        NX, NY, NZ = ctx.dims(l)
+        rho, u = synth.taylor_green_3d(NY, 0.03, shape=(NX, NY, NZ))
+        lbm.lbm_init_equilibrium(ctx, l, rho, u)
+    lbm.lbm_step(ctx, steps)
+    out = [lbm.lbm_get_raw_state(ctx, l) for l in range(2)]
+    close(ctx)
+    return out
+
+
 @pytest.mark.parametrize("model", MODELS)
-def test_checkpoint_resume_is_bitwise(model):
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+def test_results_do_not_depend_on_threads_or_grid(model, storage, monkeypatch):
+    """The thread count per CTA and the grid (one CTA per block or a
+    persistent grid) do not change a single bit of a nested run with inflow.
+    (Kernel variants compiled for another register cap may round a few
+    operations differently: the compiler contracts multiply-adds per variant.)"""
+    lbm = gpu()
+    for group in SHAPE_GROUPS:
+        out = [run_with_shape(lbm, monkeypatch, sh, model, storage) for sh in group]
+        for sh, o in zip(group[1:], out[1:]):
+            for l in range(2):
+                assert np.array_equal(o[l], out[0][l]), (sh, l)
+
+
+def test_launch_shape_override_rejects_unlisted_shapes(monkeypatch):
+    lbm = gpu()
+    monkeypatch.setenv("LBM_LAUNCH_SHAPE", "96,1,0")
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create("d3q27", "f32", (2, 1, 1), True, [], 1.5, 0.0)
+    assert e.value.status == lbm.LBM_ERR_ARG
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_checkpoint_resume_is_bitwise(model, monkeypatch):
     """The raw state of every level (distributions and, for nested D3Q19, the
     Smagorinsky strain carried across levels) plus the step counter resume a
     nested run with inflow bit for bit."""
     lbm = gpu()
     nb, ref = jet_grid(2)
     a = lbm.lbm_create(model, "f32", nb, False, ref, 1.8, 0.18)
+    # the resumed context runs the same kernel variant as the saved one
+    t, m, c = lbm.lbm_get_tuning(a)
+    monkeypatch.setenv("LBM_LAUNCH_SHAPE", f"{t},{m},{int(c > 0)}")
     lbm.lbm_set_inflow(a, 8.0, 8.0, 8.0, 0.05, 0.01, 21)
     lbm.lbm_step(a, 3)
     raw = [lbm.lbm_get_raw_state(a, l) for l in range(2)]
