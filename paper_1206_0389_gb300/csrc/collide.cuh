@@ -128,25 +128,30 @@ __device__ __forceinline__ void moments19(const T* g, T& drho, T& ux, T& uy, T& 
 // isotropic to fourth order, sum_i e_a e_b f_eq_i = drho/3 delta_ab + u_a u_b,
 // so Pi^neq = sum e e f - drho/3 I - u u without forming f - f_eq per link.
 // Returns |S| = 3 Q / (2 tau_total) (Eq. eqStrainRate, lattice units).
-template <class T>
+// Scaled: g holds g_i / w_i on entry and exit (the FP16 storage form); the
+// weights then enter as constant factors of the sums and of the output
+// terms instead of one multiply per population each way.
+template <class T, bool Scaled = false>
 __device__ __forceinline__ T collide19(T* g, T tau0, T cs2_18) {
   T sp[9], dp[9];
   static_for<9>([&](auto p) {
     sp[p] = g[2 * p + 1] + g[2 * p + 2];
     dp[p] = g[2 * p + 1] - g[2 * p + 2];
   });
-  T drho = g[0], ux = T(0), uy = T(0), uz = T(0);
+  T drho = Scaled ? T(D3Q19::w(0)) * g[0] : g[0];
+  T ux = T(0), uy = T(0), uz = T(0);
   T sxx = T(0), syy = T(0), szz = T(0), sxy = T(0), sxz = T(0), syz = T(0);
   static_for<9>([&](auto p) {
     constexpr int i = 2 * p + 1;
     constexpr int x = D3Q19::ex(i), y = D3Q19::ey(i), z = D3Q19::ez(i);
-    drho += sp[p];
-    if constexpr (x != 0) { ux += T(x) * dp[p]; sxx += sp[p]; }
-    if constexpr (y != 0) { uy += T(y) * dp[p]; syy += sp[p]; }
-    if constexpr (z != 0) { uz += T(z) * dp[p]; szz += sp[p]; }
-    if constexpr (x * y != 0) sxy += T(x * y) * sp[p];
-    if constexpr (x * z != 0) sxz += T(x * z) * sp[p];
-    if constexpr (y * z != 0) syz += T(y * z) * sp[p];
+    constexpr double ws = Scaled ? D3Q19::w(i) : 1.0;
+    drho += T(ws) * sp[p];
+    if constexpr (x != 0) { ux += T(x * ws) * dp[p]; sxx += T(ws) * sp[p]; }
+    if constexpr (y != 0) { uy += T(y * ws) * dp[p]; syy += T(ws) * sp[p]; }
+    if constexpr (z != 0) { uz += T(z * ws) * dp[p]; szz += T(ws) * sp[p]; }
+    if constexpr (x * y != 0) sxy += T(x * y * ws) * sp[p];
+    if constexpr (x * z != 0) sxz += T(x * z * ws) * sp[p];
+    if constexpr (y * z != 0) syz += T(y * z * ws) * sp[p];
   });
   const T d3 = drho * T(1.0 / 3.0);
   const T pxx = sxx - d3 - ux * ux, pyy = syy - d3 - uy * uy, pzz = szz - d3 - uz * uz;
@@ -156,10 +161,13 @@ __device__ __forceinline__ T collide19(T* g, T tau0, T cs2_18) {
   const T tau = T(0.5) * (tau0 + sqrt(tau0 * tau0 + cs2_18 * Qn));
   const T k = T(1) - T(1) / tau;
   const T tr3 = (pxx + pyy + pzz) * T(1.0 / 3.0);
-  const T ax = T(0.5) * k * (pxx - tr3), ay = T(0.5) * k * (pyy - tr3), az = T(0.5) * k * (pzz - tr3);
-  const T dxy = T(0.25) * k * pxy, dxz = T(0.25) * k * pxz, dyz = T(0.25) * k * pyz;
+  // shear projections 1/2 (axis links) and 1/4 (diagonal links), divided by
+  // the link weights 1/18 and 1/36 when scaled
+  const T cA = Scaled ? T(9) : T(0.5), cD = Scaled ? T(9) : T(0.25);
+  const T ax = cA * k * (pxx - tr3), ay = cA * k * (pyy - tr3), az = cA * k * (pzz - tr3);
+  const T dxy = cD * k * pxy, dxz = cD * k * pxz, dyz = cD * k * pyz;
   const T base = drho - T(1.5) * (ux * ux + uy * uy + uz * uz);
-  g[0] = T(D3Q19::w(0)) * base;
+  g[0] = Scaled ? base : T(D3Q19::w(0)) * base;
   static_for<9>([&](auto p) {
     constexpr int i = 2 * p + 1;
     constexpr int x = D3Q19::ex(i), y = D3Q19::ey(i), z = D3Q19::ez(i);
@@ -174,8 +182,14 @@ __device__ __forceinline__ T collide19(T* g, T tau0, T cs2_18) {
     else if constexpr (z == 0) proj = T(x * y) * dxy;
     else if constexpr (y == 0) proj = T(x * z) * dxz;
     else proj = T(y * z) * dyz;
-    const T sym = w * (base + T(4.5) * eu * eu) + proj;
-    const T asym = (T(3) * w) * eu;
+    T sym, asym;
+    if constexpr (Scaled) {
+      sym = base + T(4.5) * eu * eu + proj;
+      asym = T(3) * eu;
+    } else {
+      sym = w * (base + T(4.5) * eu * eu) + proj;
+      asym = (T(3) * w) * eu;
+    }
     g[i] = sym + asym;
     g[i + 1] = sym - asym;
   });
@@ -339,7 +353,10 @@ __device__ __forceinline__ void collide27(T* g, T omega, T Fx, T Fy, T Fz) {
 // keeps f* - w free of cancellation:
 //   f*_i - w_i = drho W_i + rho (dx Py Pz... expanded) + k_xy psi_x psi_y phi_z + ...
 // (the paper notes that fixed rates remove most of the FCLB flops).
-template <class T, bool Force>
+// Scaled: g holds g_i / w_i on entry and exit (the FP16 storage form); the
+// product weights w_i = w1_x w1_y w1_z then enter once per z-line on input
+// and once per (e_y, e_z) pair and per e_x factor on output.
+template <class T, bool Force, bool Scaled = false>
 __device__ __forceinline__ void collide27_closed(T* g, T omega, T Fx, T Fy, T Fz) {
   // ---- zeroth, first and second raw moments of g by a z, y, x collapse
   T m0[3][3], dz[3][3], sz[3][3];  // per (ex, ey): sum, difference, sum of ends along z
@@ -350,9 +367,16 @@ __device__ __forceinline__ void collide27_closed(T* g, T omega, T Fx, T Fy, T Fz
       const T lo = g[D3Q27::index(a - 1, b - 1, -1)];
       const T mi = g[D3Q27::index(a - 1, b - 1, 0)];
       const T hi = g[D3Q27::index(a - 1, b - 1, 1)];
-      sz[a][b] = hi + lo;
-      dz[a][b] = hi - lo;
-      m0[a][b] = sz[a][b] + mi;
+      if constexpr (Scaled) {
+        const T ce = T(w1(a) * w1(b) * w1(0)), cm = T(w1(a) * w1(b) * w1(1));
+        sz[a][b] = ce * (hi + lo);
+        dz[a][b] = ce * (hi - lo);
+        m0[a][b] = sz[a][b] + cm * mi;
+      } else {
+        sz[a][b] = hi + lo;
+        dz[a][b] = hi - lo;
+        m0[a][b] = sz[a][b] + mi;
+      }
     }
   T M0[3], My[3], Myy[3], Dz[3], Dyz[3], Szz[3];
 #pragma unroll
@@ -420,26 +444,54 @@ __device__ __forceinline__ void collide27_closed(T* g, T omega, T Fx, T Fy, T Fz
     }
   }
   // ---- per (e_y, e_z) pair, then per e_x
+  if constexpr (Scaled) {
+    // the x factors divided by w1_x once
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      dl[0][a] *= T(1.0 / w1(a));
+      ps[0][a] *= T(1.0 / w1(a));
+      ph[0][a] *= T(1.0 / w1(a));
+      if constexpr (Force) ch[0][a] *= T(1.0 / w1(a));
+    }
+  }
 #pragma unroll
   for (int b = 0; b < 3; ++b)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const T P = ph[1][b] * ph[2][c];                            // phi_y phi_z
       const T Qd = T(w1(b)) * dl[2][c] + dl[1][b] * ph[2][c];     // phi_y phi_z - w1_y w1_z
-      const T rP = rho * P, rQ = rho * Qd;
-      const T R = kxy * ps[1][b] * ph[2][c] + kxz * ph[1][b] * ps[2][c];
-      const T Sy = kyz * ps[1][b] * ps[2][c];
+      T rP = rho * P, rQ = rho * Qd;
+      T R = kxy * ps[1][b] * ph[2][c] + kxz * ph[1][b] * ps[2][c];
+      T Sy = kyz * ps[1][b] * ps[2][c];
       T Fp = T(0), Gp = T(0);
       if constexpr (Force) {
         Fp = T(0.5) * Fx * ch[1][b] * ch[2][c];
         Gp = T(0.5) * Fy * ps[1][b] * ch[2][c] + T(0.5) * Fz * ch[1][b] * ps[2][c];
       }
+      if constexpr (Scaled) {
+        const T ibc = T(1.0 / (w1(b) * w1(c)));
+        rP *= ibc;
+        R *= ibc;
+        Sy *= ibc;
+        if constexpr (Force) {
+          Fp *= ibc;
+          Gp *= ibc;
+        }
+        const T base = drho + ibc * rQ;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const T W = T(w1(a) * w1(b) * w1(c));
-        T v = drho * W + dl[0][a] * rP + T(w1(a)) * rQ + ps[0][a] * R + ph[0][a] * Sy;
-        if constexpr (Force) v += ps[0][a] * Fp + ch[0][a] * Gp;
-        g[D3Q27::index(a - 1, b - 1, c - 1)] = v;
+        for (int a = 0; a < 3; ++a) {
+          T v = base + dl[0][a] * rP + ps[0][a] * R + ph[0][a] * Sy;
+          if constexpr (Force) v += ps[0][a] * Fp + ch[0][a] * Gp;
+          g[D3Q27::index(a - 1, b - 1, c - 1)] = v;
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const T W = T(w1(a) * w1(b) * w1(c));
+          T v = drho * W + dl[0][a] * rP + T(w1(a)) * rQ + ps[0][a] * R + ph[0][a] * Sy;
+          if constexpr (Force) v += ps[0][a] * Fp + ch[0][a] * Gp;
+          g[D3Q27::index(a - 1, b - 1, c - 1)] = v;
+        }
       }
     }
 }

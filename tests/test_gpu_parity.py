@@ -34,12 +34,19 @@ def close(ctx):
 
 # ---------------------------------------------------------------- uniform grids
 
+# every compiled stream-collide variant: no register cap, 64-register cap
+# (one CTA per block and persistent)
+VARIANTS = ["128,1,0", "128,8,0", "256,4,1"]
+
+
 @pytest.mark.parametrize("model", MODELS)
 @pytest.mark.parametrize("nb", [(3, 2, 1), (1, 1, 1), (2, 3, 5)])
-def test_single_step_f64(model, nb):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_single_step_f64(model, nb, variant, monkeypatch):
     """One stream-collide step from a random far-from-equilibrium state,
     ragged block counts (several CTAs and a partial last wave) and the
     single-block grid whose neighbours are all itself."""
+    monkeypatch.setenv("LBM_LAUNCH_SHAPE", variant)
     ctx, orc = make_pair(model, "f64", nb, omega=1.7, cs=0.18)
     upload_same_state(ctx, orc, [random_state(model, dims(nb), 11, 0.3)])
     gpu().lbm_step(ctx, 1)
@@ -50,7 +57,9 @@ def test_single_step_f64(model, nb):
 
 
 @pytest.mark.parametrize("model", MODELS)
-def test_single_step_f32(model):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_single_step_f32(model, variant, monkeypatch):
+    monkeypatch.setenv("LBM_LAUNCH_SHAPE", variant)
     nb = (3, 2, 2)
     ctx, orc = make_pair(model, "f32", nb, omega=1.9, cs=0.1)
     upload_same_state(ctx, orc, [random_state(model, dims(nb), 5, 0.3)])
@@ -62,7 +71,9 @@ def test_single_step_f32(model):
 
 
 @pytest.mark.parametrize("model", MODELS)
-def test_single_step_f16(model):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_single_step_f16(model, variant, monkeypatch):
+    monkeypatch.setenv("LBM_LAUNCH_SHAPE", variant)
     nb = (2, 2, 2)
     lbm = gpu()
     ctx, orc = make_pair(model, "f16", nb, omega=1.5, cs=0.1)
