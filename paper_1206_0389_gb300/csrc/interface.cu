@@ -129,7 +129,13 @@ __global__ void __launch_bounds__(kC2FMaxItems) k_c2f(const C2FArgs a) {
   constexpr int Q = M::Q;
   constexpr int QS = Q * kCells;
   constexpr int MC = c2f_max_cells(std::is_same<S, double>::value ? LBM_F64 : LBM_F32);
-  __shared__ T sv[Q * MC];
+  // one row of Q values per staged cell, padded to whole 16-byte vectors:
+  // rows are written and read with 16-byte shared accesses (the row stride
+  // of 20 or 28 words keeps the lanes of a quarter warp on distinct banks)
+  constexpr int VW = 16 / int(sizeof(T));
+  constexpr int QP = (Q + VW - 1) / VW * VW;
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  __shared__ __align__(16) T sv[MC * QP];
   __shared__ T sS[MC];
   int g = blockIdx.x;
   const C2FLevel L = pick_level<C2FLevel>(a, g);
@@ -148,7 +154,18 @@ __global__ void __launch_bounds__(kC2FMaxItems) k_c2f(const C2FArgs a) {
     if (L.s == 1) {
       static_for<Q>([&](auto i) { v[i] = T(0.5) * (v[i] + St::template get<Q, i>(cn + o + int(i) * kCells)); });
     }
-    static_for<Q>([&](auto i) { sv[int(i) * MC + j] = v[i]; });
+    static_for<QP / VW>([&](auto b) {
+      T t[VW];
+      static_for<VW>([&](auto e) {
+        constexpr int i = int(b) * VW + int(e);
+        if constexpr (i < Q) t[e] = v[i];
+        else t[e] = T(0);
+      });
+      V vec;
+      if constexpr (VW == 4) vec = make_float4(t[0], t[1], t[2], t[3]);
+      else vec = make_double2(t[0], t[1]);
+      *reinterpret_cast<V*>(sv + j * QP + int(b) * VW) = vec;
+    });
     if (L.a_old != nullptr) {
       const int64_t jj = int64_t(cl.cblock) * kCells + cl.ccell;
       T sj = reinterpret_cast<const T*>(L.a_old)[jj];
@@ -168,9 +185,16 @@ __global__ void __launch_bounds__(kC2FMaxItems) k_c2f(const C2FArgs a) {
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const T W = ((k & 4) ? tz : T(1) - tz) * ((k & 2) ? ty : T(1) - ty) * ((k & 1) ? tx : T(1) - tx);
-    const int sl = it.slot[k];
-    static_for<Q>([&](auto i) { F[i] += W * sv[int(i) * MC + sl]; });
-    if (L.a_old != nullptr) Sh += W * sS[sl];
+    const T* row = sv + int(it.slot[k]) * QP;
+    static_for<QP / VW>([&](auto b) {
+      const V vec = *reinterpret_cast<const V*>(row + int(b) * VW);
+      const T* t = reinterpret_cast<const T*>(&vec);
+      static_for<VW>([&](auto e) {
+        constexpr int i = int(b) * VW + int(e);
+        if constexpr (i < Q) F[i] += W * t[e];
+      });
+    });
+    if (L.a_old != nullptr) Sh += W * sS[it.slot[k]];
   }
   T rl, ux, uy, uz;
   M::moments(F, rl, ux, uy, uz);
@@ -293,23 +317,24 @@ __global__ void __launch_bounds__(128) k_bc(const BCArgs a) {
   const Lane<T, Q> ln(q);
   const T g = act ? lane_load(src + q * kCells, ln) : T(0);
   const T rl = warp_sum(g);
-  const double yc = (double(it.y) + 0.5) * L.inv_scale;
-  const double zc = (double(it.z) + 0.5) * L.inv_scale;
-  const double dy = yc - a.y0, dz = zc - a.z0;
-  double ux = 0.0, uy = 0.0, uz = 0.0;
-  if (dy * dy + dz * dz < a.r2) {
-    const long long step = *a.step;
-    const long long cell = (long long)it.y + (long long)L.NY * it.z;
-    // lanes 0..2 draw one component each
-    const double xi = inflow_xi(a.seed, step, L.level, L.substep, cell, q < 3 ? q : 0);
-    const double xx = __shfl_sync(0xffffffffu, xi, 0);
-    const double xy = __shfl_sync(0xffffffffu, xi, 1);
-    const double xz = __shfl_sync(0xffffffffu, xi, 2);
-    ux = a.u_in * (1.0 + a.perturb * xx);
-    uy = a.u_in * a.perturb * xy;
-    uz = a.u_in * a.perturb * xz;
+  // the disc test and the draws run in double on lanes 0..2 only (lane c
+  // computes velocity component c): FP64 throughput is scarce on this part,
+  // and warp-wide double arithmetic cost more than the loads
+  T uc = T(0);
+  if (q < 3) {
+    const double yc = (double(it.y) + 0.5) * L.inv_scale;
+    const double zc = (double(it.z) + 0.5) * L.inv_scale;
+    const double dy = yc - a.y0, dz = zc - a.z0;
+    if (dy * dy + dz * dz < a.r2) {
+      const long long cell = (long long)it.y + (long long)L.NY * it.z;
+      const double xi = inflow_xi(a.seed, *a.step, L.level, L.substep, cell, q);
+      uc = T(q == 0 ? a.u_in * (1.0 + a.perturb * xi) : a.u_in * a.perturb * xi);
+    }
   }
-  if (act && ln.x == 1) lane_store(dst + q * kCells, ln, lane_feq<M>(rl, T(ux), T(uy), T(uz), ln));
+  const T ux = __shfl_sync(0xffffffffu, uc, 0);
+  const T uy = __shfl_sync(0xffffffffu, uc, 1);
+  const T uz = __shfl_sync(0xffffffffu, uc, 2);
+  if (act && ln.x == 1) lane_store(dst + q * kCells, ln, lane_feq<M>(rl, ux, uy, uz, ln));
 }
 
 __global__ void k_step_inc(long long* step) { *step += 1; }
