@@ -118,10 +118,10 @@ __device__ __forceinline__ T quad_sum(T v) {
 
 // One CTA per chunk (kC2FMaxItems threads): stage the chunk's distinct
 // coarse stencil cells in shared memory (for substep 1 already averaged over
-// t and t+1), population by population so that consecutive threads read
-// consecutive cells; then one thread per ghost cell interpolates from shared
-// memory.  The distinct cells of a chunk number about a quarter of its
-// 8 x items stencil references, and every global read is a coalesced run.
+// t and t+1), one thread per cell with all Q loads in flight (consecutive
+// threads read consecutive cells of the address-sorted list); then one thread
+// per ghost cell interpolates from shared memory.  The distinct cells of a
+// chunk number about a quarter of its 8 x items stencil references.
 template <class M, class S>
 __global__ void __launch_bounds__(kC2FMaxItems) k_c2f(const C2FArgs a) {
   using St = Store<S>;
