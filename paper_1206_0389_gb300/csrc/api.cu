@@ -44,6 +44,7 @@ struct DevLevel {
   C2FItem* c2f = nullptr;
   C2FChunk* c2f_chunks = nullptr;
   C2FCell* c2f_cells = nullptr;
+  BCItem* c2f_bc = nullptr;
   F2CItem* f2c = nullptr;
   BCItem* bc = nullptr;
   double* force = nullptr;
@@ -57,6 +58,10 @@ struct lbm_ctx {
   double omega = 1.0, cs = 0.0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // second stream and events for the branch of the coarse-step graph that
+  // runs the inflow launch beside the coarse-to-fine launch
+  cudaStream_t side = nullptr;
+  std::vector<cudaEvent_t> fork_join;
   int device = 0, sms = 1;
   std::vector<DevLevel> dl;
   WorkItem* items = nullptr;          // merged lists for each lowest level
@@ -131,6 +136,7 @@ void free_all(lbm_ctx* c) {
     cudaFree(d.c2f);
     cudaFree(d.c2f_chunks);
     cudaFree(d.c2f_cells);
+    cudaFree(d.c2f_bc);
     cudaFree(d.f2c);
     cudaFree(d.bc);
     cudaFree(d.force);
@@ -147,6 +153,8 @@ void free_all(lbm_ctx* c) {
   cudaFree(c->adj_lam[0]);
   cudaFree(c->adj_lam[1]);
   cudaFree(c->adj_gF);
+  for (cudaEvent_t e : c->fork_join) cudaEventDestroy(e);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -174,6 +182,13 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
       op.kind = Op::C2F;
       C2FArgs& a = op.ca;
       a.cs2_3 = cs2_3;
+      a.step = c->d_step;
+      a.y0 = c->y0;
+      a.z0 = c->z0;
+      a.r2 = (0.5 * c->diameter) * (0.5 * c->diameter);
+      a.u_in = c->u_in;
+      a.perturb = c->perturb;
+      a.seed = c->seed;
       for (int l = std::max(lmin, 1); l < L; ++l) {
         const int s = sub(l) % 2;
         const LevelPlan& fp = c->plan.lv[l];
@@ -183,6 +198,11 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
         v.chunks = c->dl[l].c2f_chunks;
         v.items = c->dl[l].c2f;
         v.cells = c->dl[l].c2f_cells;
+        v.bc = c->dl[l].c2f_bc;
+        v.level = l;
+        v.substep = sub(l);
+        v.NY = fp.NY;
+        v.inv_scale = std::ldexp(1.0, -l);
         v.n = int(fp.c2f_chunks.size());
         const int pc = par[l - 1];
         v.c_old = c->dl[l - 1].f[s == 0 ? pc : 1 - pc];
@@ -279,16 +299,17 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
   return ops;
 }
 
-cudaError_t run_op(lbm_ctx* c, const Op& op) {
+cudaError_t run_op(lbm_ctx* c, const Op& op, cudaStream_t st) {
   switch (op.kind) {
-    case Op::UPDATE: return launch_update(c->model, c->storage, op.ua, c->threads, c->minb, c->ctas, c->stream);
-    case Op::C2F: return launch_c2f(c->model, c->storage, op.ca, c->stream);
-    case Op::F2C: return launch_f2c(c->model, c->storage, op.fa, c->stream);
-    case Op::BC: return launch_bc(c->model, c->storage, op.ba, c->stream);
-    case Op::INC: return launch_step_inc(c->d_step, c->stream);
+    case Op::UPDATE: return launch_update(c->model, c->storage, op.ua, c->threads, c->minb, c->ctas, st);
+    case Op::C2F: return launch_c2f(c->model, c->storage, op.ca, st);
+    case Op::F2C: return launch_f2c(c->model, c->storage, op.fa, st);
+    case Op::BC: return launch_bc(c->model, c->storage, op.ba, st);
+    case Op::INC: return launch_step_inc(c->d_step, st);
   }
   return cudaErrorInvalidValue;
 }
+cudaError_t run_op(lbm_ctx* c, const Op& op) { return run_op(c, op, c->stream); }
 
 int op_kind_index(const Op& op) {
   switch (op.kind) {
@@ -334,9 +355,25 @@ int build_graphs(lbm_ctx* ctx) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (const Op& op : ops) {
-      e = run_op(ctx, op);
-      if (e != cudaSuccess) break;
+    size_t ev = 0;
+    for (size_t k = 0; k < ops.size() && e == cudaSuccess; ++k) {
+      // the inflow launch after a coarse-to-fine launch touches other cells
+      // (inflow ghosts fed by ghost cells are written by the latter), so the
+      // graph runs the two side by side
+      if (ops[k].kind == Op::C2F && k + 1 < ops.size() && ops[k + 1].kind == Op::BC &&
+          ev + 1 < ctx->fork_join.size()) {
+        cudaEvent_t fork = ctx->fork_join[ev++], join = ctx->fork_join[ev++];
+        if ((e = cudaEventRecord(fork, ctx->stream)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->side, fork, 0)) != cudaSuccess ||
+            (e = run_op(ctx, ops[k + 1], ctx->side)) != cudaSuccess ||
+            (e = run_op(ctx, ops[k], ctx->stream)) != cudaSuccess ||
+            (e = cudaEventRecord(join, ctx->side)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->stream, join, 0)) != cudaSuccess)
+          break;
+        ++k;
+        continue;
+      }
+      e = run_op(ctx, ops[k]);
     }
     cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
     if (e != cudaSuccess) {
@@ -576,6 +613,13 @@ int lbm_create(lbm_ctx** out, lbm_model model, lbm_storage storage, const lbm_gr
     if (ce != cudaSuccess) return bail(LBM_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(ce));
     ctx->own_stream = true;
   }
+  ce = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+  if (ce != cudaSuccess) return bail(LBM_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(ce));
+  ctx->fork_join.assign(2 << (ctx->L - 1), nullptr);
+  for (cudaEvent_t& e : ctx->fork_join) {
+    ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    if (ce != cudaSuccess) return bail(LBM_ERR_CUDA, std::string("event: ") + cudaGetErrorString(ce));
+  }
   const size_t sb = storage_bytes(ctx->storage), rb = real_bytes(ctx->storage);
   const bool aux = ctx->model == LBM_D3Q19_MRT_LES && ctx->L > 1;
   ctx->dl.resize(ctx->L);
@@ -601,6 +645,7 @@ int lbm_create(lbm_ctx** out, lbm_model model, lbm_storage storage, const lbm_gr
     if ((ce = upload(&d.kind, lp.kind)) != cudaSuccess || (ce = upload(&d.c2f, lp.c2f)) != cudaSuccess ||
         (ce = upload(&d.c2f_chunks, lp.c2f_chunks)) != cudaSuccess ||
         (ce = upload(&d.c2f_cells, lp.c2f_cells)) != cudaSuccess ||
+        (ce = upload(&d.c2f_bc, lp.c2f_bc)) != cudaSuccess ||
         (ce = upload(&d.f2c, lp.f2c)) != cudaSuccess || (ce = upload(&d.bc, lp.bc)) != cudaSuccess)
       return bail(LBM_ERR_OOM, std::string("plan tables: ") + cudaGetErrorString(ce));
     const int16_t moff = int16_t(masks.size() / 16);

@@ -94,6 +94,42 @@ __device__ __forceinline__ T lane_feq(T rl, T ux, T uy, T uz, const Lane<T, Q>& 
 // by two xor shuffles, and lane r stores the populations i with i % 4 == r.
 constexpr int kLanes = 4;
 
+// SplitMix64 (Steele, Lea & Flood 2014): advance by the golden gamma, then mix.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// xi in [-1, 1) for one boundary value: chain over (seed, coarse step,
+// level << 32 | substep, cell, component)
+__device__ __forceinline__ double inflow_xi(unsigned long long seed, long long step, int level,
+                                            int substep, long long cell, int comp) {
+  unsigned long long h = splitmix64(seed);
+  h = splitmix64(h ^ (unsigned long long)step);
+  h = splitmix64(h ^ (((unsigned long long)level << 32) | (unsigned long long)substep));
+  h = splitmix64(h ^ (unsigned long long)cell);
+  h = splitmix64(h ^ (unsigned long long)comp);
+  return 2.0 * double(h >> 11) * 0x1.0p-53 - 1.0;
+}
+
+// inflow velocity component c (0, 1, 2) of face cell (y, z) of a level at
+// (coarse step, level, substep): the disc velocity with its perturbation,
+// zero outside the disc (double: the disc test decides a bit)
+__device__ __forceinline__ double inflow_u(const long long* step, double y0, double z0, double r2,
+                                           double u_in, double perturb, unsigned long long seed,
+                                           int level, int substep, int NY, double inv_scale, int y,
+                                           int z, int c) {
+  const double yc = (double(y) + 0.5) * inv_scale;
+  const double zc = (double(z) + 0.5) * inv_scale;
+  const double dy = yc - y0, dz = zc - z0;
+  if (!(dy * dy + dz * dz < r2)) return 0.0;
+  const long long cell = (long long)y + (long long)NY * z;
+  const double xi = inflow_xi(seed, *step, level, substep, cell, c);
+  return c == 0 ? u_in * (1.0 + perturb * xi) : u_in * perturb * xi;
+}
+
 // the level that owns global item g of a multi-level launch (a register
 // copy: the unrolled selects keep the launch parameters in the constant
 // bank); g becomes the level-local index
@@ -208,6 +244,22 @@ __global__ void __launch_bounds__(kC2FMaxItems) k_c2f(const C2FArgs a) {
     if ((it.need >> int(i)) & 1u) St::template put<Q, i>(fd + int(i) * kCells, feq[i] + rr * (F[i] - feq[i]));
   });
   if (L.fa_dst != nullptr) reinterpret_cast<T*>(L.fa_dst)[int64_t(it.fblock) * kCells + it.fcell] = Sh / T(2);
+  if (it.bc >= 0) {
+    // the inflow ghost fed by this ghost cell: f_eq(rho of the cell, u_bc);
+    // the cell's density is that of F^ (f_eq and F^ - f_eq carry rho^, 0)
+    const BCItem b = L.bc[it.bc];
+    T ub[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      ub[c] = T(inflow_u(a.step, a.y0, a.z0, a.r2, a.u_in, a.perturb, a.seed, L.level, L.substep, L.NY,
+                         L.inv_scale, b.y, b.z, c));
+    T fb[Q];
+    M::feq(rl, ub[0], ub[1], ub[2], fb);
+    S* gd = reinterpret_cast<S*>(L.f_dst) + int64_t(b.gblock) * QS + b.gcell;
+    static_for<Q>([&](auto i) {
+      if constexpr (Lattice<Q>::ex(i) == 1) St::template put<Q, i>(gd + int(i) * kCells, fb[i]);
+    });
+  }
 }
 
 // two adjacent stored values starting at an even index: one aligned load
@@ -279,26 +331,6 @@ __global__ void __launch_bounds__(128) k_f2c(const F2CArgs a) {
   if (L.ca_dst != nullptr && r == 0) reinterpret_cast<T*>(L.ca_dst)[int64_t(it.cblock) * kCells + it.ccell] = accS / T(8);
 }
 
-// SplitMix64 (Steele, Lea & Flood 2014): advance by the golden gamma, then mix.
-__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
-  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-// xi in [-1, 1) for one boundary value: chain over (seed, coarse step,
-// level << 32 | substep, cell, component)
-__device__ __forceinline__ double inflow_xi(unsigned long long seed, long long step, int level,
-                                            int substep, long long cell, int comp) {
-  unsigned long long h = splitmix64(seed);
-  h = splitmix64(h ^ (unsigned long long)step);
-  h = splitmix64(h ^ (((unsigned long long)level << 32) | (unsigned long long)substep));
-  h = splitmix64(h ^ (unsigned long long)cell);
-  h = splitmix64(h ^ (unsigned long long)comp);
-  return 2.0 * double(h >> 11) * 0x1.0p-53 - 1.0;
-}
-
 template <class M, class S>
 __global__ void __launch_bounds__(128) k_bc(const BCArgs a) {
   using St = Store<S>;
@@ -321,16 +353,9 @@ __global__ void __launch_bounds__(128) k_bc(const BCArgs a) {
   // computes velocity component c): FP64 throughput is scarce on this part,
   // and warp-wide double arithmetic cost more than the loads
   T uc = T(0);
-  if (q < 3) {
-    const double yc = (double(it.y) + 0.5) * L.inv_scale;
-    const double zc = (double(it.z) + 0.5) * L.inv_scale;
-    const double dy = yc - a.y0, dz = zc - a.z0;
-    if (dy * dy + dz * dz < a.r2) {
-      const long long cell = (long long)it.y + (long long)L.NY * it.z;
-      const double xi = inflow_xi(a.seed, *a.step, L.level, L.substep, cell, q);
-      uc = T(q == 0 ? a.u_in * (1.0 + a.perturb * xi) : a.u_in * a.perturb * xi);
-    }
-  }
+  if (q < 3)
+    uc = T(inflow_u(a.step, a.y0, a.z0, a.r2, a.u_in, a.perturb, a.seed, L.level, L.substep, L.NY, L.inv_scale,
+                    it.y, it.z, q));
   const T ux = __shfl_sync(0xffffffffu, uc, 0);
   const T uy = __shfl_sync(0xffffffffu, uc, 1);
   const T uz = __shfl_sync(0xffffffffu, uc, 2);

@@ -75,6 +75,8 @@ struct C2FItem {
   uint32_t need;      // bit i: population i is pulled by an updated cell of the level
   uint16_t slot[8];   // stencil cells (dz, dy, dx order, dx fastest; 0 = lower,
                       // 1 = upper index) as indices into the chunk's cell list
+  int32_t bc;         // the inflow ghost that takes its density from this ghost
+                      // cell (index into the level's c2f_bc list), or -1
 };
 // chunk limits (distinct cells x Q values of the compute type stay at 27 KB
 // of shared memory)
@@ -113,8 +115,11 @@ struct C2FLevel {
   const C2FChunk* chunks;
   const C2FItem* items;
   const C2FCell* cells;
+  const BCItem* bc;   // inflow ghosts whose source is a ghost cell of this level
   int n;              // chunks
   int s;              // fine substep 0 or 1
+  int level, substep, NY;  // for those inflow ghosts (substep = index within the coarse step)
+  double inv_scale;        // 2^-level
   const void* c_old;  // coarse storage at t
   const void* c_new;  // coarse storage at t+1 (used when s == 1)
   const void* a_old;  // coarse |S| at t (LES) or nullptr
@@ -128,6 +133,9 @@ struct C2FArgs {
   int nlv;
   int n;           // chunks of all levels
   double cs2_3;    // 3 Cs^2
+  const long long* step;  // inflow (see BCArgs)
+  double y0, z0, r2, u_in, perturb;
+  unsigned long long seed;
 };
 
 struct F2CLevel {

@@ -334,7 +334,10 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
               it.scell = int16_t(sc);
               it.y = 8 * by + cy;
               it.z = 8 * bz + cz;
-              lp.bc.push_back(it);
+              // a coarse-to-fine ghost source only gets its value in the
+              // same substep: that kernel writes this inflow ghost too
+              if (lp.kind[int64_t(sb) * 512 + sc] == K_GHOST) lp.c2f_bc.push_back(it);
+              else lp.bc.push_back(it);
             }
         }
     }
@@ -382,6 +385,7 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
             }
             Ghost gh{};
             C2FItem& it = gh.it;
+            it.bc = -1;
             it.fblock = b;
             it.fcell = int16_t(cc);
             it.tbits = tb;
@@ -456,6 +460,15 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
       g0 = g1;
     }
     if (f.c2f_cells.size() >= (size_t(1) << 31)) return "too many coarse-to-fine cells";
+    if (!f.c2f_bc.empty()) {
+      std::vector<int32_t> at(size_t(f.nblocks()) * 512, -1);
+      for (size_t k = 0; k < f.c2f.size(); ++k) at[int64_t(f.c2f[k].fblock) * 512 + f.c2f[k].fcell] = int32_t(k);
+      for (size_t j = 0; j < f.c2f_bc.size(); ++j) {
+        const int32_t k = at[int64_t(f.c2f_bc[j].sblock) * 512 + f.c2f_bc[j].scell];
+        if (k < 0) return "internal: inflow ghost source is not a coarse-to-fine ghost";
+        f.c2f[k].bc = int32_t(j);
+      }
+    }
   }
   for (int l = 0; l + 1 < L; ++l) {
     LevelPlan& c = P.lv[l];
@@ -498,7 +511,7 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
     bytes += int64_t(lp.items.size() * sizeof(WorkItem) + lp.masks.size() * 4 +
                      lp.c2f.size() * sizeof(C2FItem) + lp.c2f_chunks.size() * sizeof(C2FChunk) +
                      lp.c2f_cells.size() * sizeof(C2FCell) + lp.f2c.size() * sizeof(F2CItem) +
-                     lp.bc.size() * sizeof(BCItem));
+                     (lp.bc.size() + lp.c2f_bc.size()) * sizeof(BCItem));
   }
   P.device_bytes = bytes;
   return "";

@@ -31,7 +31,9 @@ struct LevelPlan {
   std::vector<C2FChunk> c2f_chunks;
   std::vector<C2FCell> c2f_cells;   // distinct coarse stencil cells per chunk
   std::vector<F2CItem> f2c;         // hidden cells of this level (l < L-1)
-  std::vector<BCItem> bc;           // boundary ghost cells
+  std::vector<BCItem> bc;           // inflow ghost cells
+  std::vector<BCItem> c2f_bc;       // inflow ghosts whose source is a c2f ghost cell
+                                    // (written by the coarse-to-fine kernel)
   std::vector<int32_t> block_of;    // [nbz][nby][nbx] in-domain block -> box id or -1
 
   int64_t level_blocks = 0, active_cells = 0, updated_cells = 0, hidden_cells = 0;
