@@ -24,23 +24,15 @@
 
 namespace lbm {
 
-// ---------------------------------------------------------------- warp-per-cell helpers
-// The boundary kernel gives one warp to one ghost cell and one lane to each
-// population, so every lane issues one load (the x-face cells it serves are
-// 8 elements apart, so a thread-per-cell kernel serialises 27 sector loads per
-// thread); the cell's density is a warp sum.  Each lane reads its velocity and weight once
-// (through L1: the lanes of a warp read 27 different entries, which constant
-// memory would serialise) and keeps them in registers.
+// ---------------------------------------------------------------- lane-per-population helpers
+// The inflow kernel gives each population of a ghost cell to a lane (the
+// x-face cells it serves are 8 elements apart, so a thread-per-cell kernel
+// serialises 27 sector loads per thread).  Each lane reads its velocity and
+// weight through L1 (the lanes of a warp read different entries, which
+// constant memory would serialise) and keeps them in registers.
 __device__ const int8_t g_ex[32] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, 1, -1, -1, 1, -1};
 __device__ const int8_t g_ey[32] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1, 1, 1, -1, 1, -1, 1, -1, -1};
 __device__ const int8_t g_ez[32] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1, 1, 1, 1, -1, 1, -1, -1, -1};
-
-template <class T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // velocity and weight of the lane's population (lanes >= Q get zeros)
 template <class T, int Q>
@@ -331,41 +323,64 @@ __global__ void __launch_bounds__(128) k_f2c(const F2CArgs a) {
   if (L.ca_dst != nullptr && r == 0) reinterpret_cast<T*>(L.ca_dst)[int64_t(it.cblock) * kCells + it.ccell] = accS / T(8);
 }
 
+// Inflow: eight lanes per ghost cell, four cells per warp; lane r loads the
+// source cell's populations r, r + 8, r + 16, r + 24 (the x-face cells are 8
+// elements apart, so every value costs a sector however the lanes are laid
+// out), the density is a sum over the eight lanes, and each lane writes its
+// populations with e_x = +1.
+constexpr int kBCLanes = 8;
+
 template <class M, class S>
 __global__ void __launch_bounds__(128) k_bc(const BCArgs a) {
   using St = Store<S>;
   using T = typename St::T;
   constexpr int Q = M::Q;
   constexpr int QS = Q * kCells;
-  int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int q = threadIdx.x & 31;
-  if (n >= a.n) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = t & (kBCLanes - 1);
+  const bool valid = (t / kBCLanes) < a.n;
+  int n = valid ? t / kBCLanes : a.n - 1;  // tail lanes mirror the last cell
   const BCLevel L = pick_level<BCLevel>(a, n);
   const BCItem& it = L.items[n];
-  const bool act = q < Q;
   S* f = reinterpret_cast<S*>(L.f);
   const S* src = f + int64_t(it.sblock) * QS + it.scell;
   S* dst = f + int64_t(it.gblock) * QS + it.gcell;
-  const Lane<T, Q> ln(q);
-  const T g = act ? lane_load(src + q * kCells, ln) : T(0);
-  const T rl = warp_sum(g);
-  // the disc test and the draws run in double on lanes 0..2 only (lane c
-  // computes velocity component c): FP64 throughput is scarce on this part,
-  // and warp-wide double arithmetic cost more than the loads
+  constexpr int NJ = (Q + kBCLanes - 1) / kBCLanes;
+  T part = T(0);
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const int q = r + kBCLanes * j;
+    if (q < Q) part += lane_load(src + q * kCells, Lane<T, Q>(q));
+  }
+  part += __shfl_xor_sync(0xffffffffu, part, 1);
+  part += __shfl_xor_sync(0xffffffffu, part, 2);
+  part += __shfl_xor_sync(0xffffffffu, part, 4);
+  const T rl = part;
+  // the disc test and the draws run in double on lanes 0..2 of the group
+  // only (lane c computes velocity component c): FP64 throughput is scarce
+  // on this part
   T uc = T(0);
-  if (q < 3)
+  if (r < 3)
     uc = T(inflow_u(a.step, a.y0, a.z0, a.r2, a.u_in, a.perturb, a.seed, L.level, L.substep, L.NY, L.inv_scale,
-                    it.y, it.z, q));
-  const T ux = __shfl_sync(0xffffffffu, uc, 0);
-  const T uy = __shfl_sync(0xffffffffu, uc, 1);
-  const T uz = __shfl_sync(0xffffffffu, uc, 2);
-  if (act && ln.x == 1) lane_store(dst + q * kCells, ln, lane_feq<M>(rl, ux, uy, uz, ln));
+                    it.y, it.z, r));
+  const int g0 = int(threadIdx.x & 31) & ~(kBCLanes - 1);
+  const T ux = __shfl_sync(0xffffffffu, uc, g0);
+  const T uy = __shfl_sync(0xffffffffu, uc, g0 + 1);
+  const T uz = __shfl_sync(0xffffffffu, uc, g0 + 2);
+  if (!valid) return;
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const int q = r + kBCLanes * j;
+    if (q >= Q) continue;
+    const Lane<T, Q> ln(q);
+    if (ln.x == 1) lane_store(dst + q * kCells, ln, lane_feq<M>(rl, ux, uy, uz, ln));
+  }
 }
 
 __global__ void k_step_inc(long long* step) { *step += 1; }
 
 // coarse-to-fine: one CTA per chunk; fine-to-coarse: four lanes per item, 32
-// items per CTA; boundary: one warp per item, four items per CTA
+// items per CTA; inflow: eight lanes per item, 16 items per CTA
 template <class M, class S>
 static cudaError_t c2f_ms(const C2FArgs& a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
@@ -381,7 +396,7 @@ static cudaError_t f2c_ms(const F2CArgs& a, cudaStream_t st) {
 template <class M, class S>
 static cudaError_t bc_ms(const BCArgs& a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
-  k_bc<M, S><<<(a.n + 3) / 4, 128, 0, st>>>(a);
+  k_bc<M, S><<<(a.n + 128 / kBCLanes - 1) / (128 / kBCLanes), 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 
