@@ -301,6 +301,41 @@ def test_nested_parity_f32_per_step(model):
 
 
 @pytest.mark.parametrize("model", MODELS)
+def test_nested_parity_f16_per_step(model):
+    """FP16 storage on the nested jet with inflow: one coarse step (two fine
+    substeps, both interface transfers, the inflow) from the GPU's rounded
+    state, against the float64 oracle.  Each stored value carries the
+    half-precision rounding of (f - w)/w (2^-11 relative) once per substep;
+    the bound allows four roundings of the largest deviation."""
+    lbm = gpu()
+    nb, ref = jet_grid(2)
+    ctx, orc = make_pair(model, "f16", nb, False, ref, omega=1.9, cs=0.1)
+    init_both(ctx, orc, nested_fields(orc))
+    lbm.lbm_set_inflow(ctx, 8.0, 8.0, 8.0, 0.05, 0.01, 99)
+    orc.set_inflow(8.0, 8.0, 8.0, 0.05, 0.01, 99)
+    lbm.lbm_step(ctx, 1)
+    orc.step(1)
+    for l in range(2):
+        orc.set_state(l, torch.from_numpy(lbm.lbm_get_state(ctx, l)))
+    orc.coarse_step = lbm.lbm_get_step(ctx)
+    lbm.lbm_step(ctx, 1)
+    orc.step(1)
+    from oracle.lattice import weights
+    Q = 19 if model == "d3q19" else 27
+    w = weights(Q).numpy()
+    shift = w if model == "d3q27" else np.zeros_like(w)
+    for l in range(2):
+        m = valid_mask(orc, l)
+        fg = lbm.lbm_get_state(ctx, l)[:, m]
+        fo = orc.state(l).numpy()[:, m]
+        scaled = np.abs(fo - shift[:, None]) / w[:, None]
+        err = np.abs(fg - fo) / w[:, None]
+        bound = 4 * 2.0 ** -11 * scaled.max() + 1e-6
+        assert err.max() <= bound, (l, err.max(), bound)
+    close(ctx)
+
+
+@pytest.mark.parametrize("model", MODELS)
 def test_rest_state_with_zero_inflow_stays_at_rest(model):
     lbm = gpu()
     nb, ref = jet_grid(2)
