@@ -395,6 +395,12 @@ def ours(args):
                                                      zip(["update", "c2f", "f2c", "bc", "other"], pms)},
                               "launches": [int(x) for x in pn]}), flush=True)
         return
+    if args.kernel_only and args.variant == "adjoint":
+        # the adjoint pipeline at 96^3 with a short horizon (profiling k_adjoint)
+        r = run_adjoint(lbm, torch, stream, T=32, every=8)
+        if rank == 0:
+            print(json.dumps({"kernel_only": True, "variant": "adjoint", **r}), flush=True)
+        return
     if args.kernel_only:
         model, storage = args.variant.split("_")
         r = run_uniform(lbm, torch, model, storage, field, K, W, stream)
@@ -548,7 +554,8 @@ def main():
     ap.add_argument("--kernel-only", action="store_true",
                     help="only the stream-collide steps of one variant (for ncu captures)")
     ap.add_argument("--variant", default="d3q27_f32",
-                    help="model_storage for --kernel-only, e.g. d3q19_f16")
+                    help="for --kernel-only: model_storage (e.g. d3q19_f16), jet2s_/jet3s_/jet3p_"
+                         "model_storage, or adjoint")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

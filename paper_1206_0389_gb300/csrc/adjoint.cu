@@ -301,9 +301,10 @@ __global__ void __launch_bounds__(TPB) k_adjoint(const AdjointArgs a) {
       const int64_t j = int64_t(b) * kCells + c;
       T Fx = T(0), Fy = T(0), Fz = T(0);
       if (a.force != nullptr) {
-        Fx = T(a.force[j]);
-        Fy = T(a.force[ncell + j]);
-        Fz = T(a.force[2 * ncell + j]);
+        const T* F = reinterpret_cast<const T*>(a.force);
+        Fx = F[j];
+        Fy = F[ncell + j];
+        Fz = F[2 * ncell + j];
       }
       T Fbx = T(0), Fby = T(0), Fbz = T(0);
       collide27_adjoint<T>(g, lam, T(a.omega), Fx, Fy, Fz, Fbx, Fby, Fbz);

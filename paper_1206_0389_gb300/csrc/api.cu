@@ -48,6 +48,7 @@ struct DevLevel {
   F2CItem* f2c = nullptr;
   BCItem* bc = nullptr;
   double* force = nullptr;
+  float* force_f = nullptr;  // float copy for FP32/FP16 storage (compute type)
 };
 
 }  // namespace
@@ -140,6 +141,7 @@ void free_all(lbm_ctx* c) {
     cudaFree(d.f2c);
     cudaFree(d.bc);
     cudaFree(d.force);
+    cudaFree(d.force_f);
   }
   cudaFree(c->items);
   cudaFree(c->masks);
@@ -263,7 +265,9 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
     u.nitems = int(c->list_len[lmin]);
     u.masks = c->masks;
     u.cs2_18 = 18.0 * c->cs * c->cs;
-    u.force = c->has_force ? c->dl[0].force : nullptr;
+    u.force = !c->has_force ? nullptr
+              : c->storage == LBM_F64 ? static_cast<const void*>(c->dl[0].force)
+                                       : static_cast<const void*>(c->dl[0].force_f);
     ops.push_back(up);
     for (int l = lmin; l < L; ++l) par[l] ^= 1;
     // fine-to-coarse after the second substep of each fine level: one launch
@@ -759,6 +763,11 @@ int lbm_set_force(lbm_ctx* ctx, const double* F) {
   const double* hin[3] = {F, F + n, F + 2 * n};
   int rc = slab_transfer(ctx, 0, SLAB_SET_FORCE, hin, nullptr, 3);
   if (rc) return rc;
+  if (ctx->storage != LBM_F64) {
+    const long long nf = (long long)lp.nblocks() * 512 * 3;
+    if (!ctx->dl[0].force_f) CK(cudaMalloc(&ctx->dl[0].force_f, size_t(nf) * sizeof(float)));
+    CK(launch_to_float(ctx->dl[0].force, ctx->dl[0].force_f, nf, ctx->stream));
+  }
   ctx->has_force = true;
   ctx->graphs_valid = false;
   return LBM_OK;
@@ -1086,7 +1095,9 @@ int lbm_adjoint_backward(lbm_ctx* ctx, const double* dLdf_T, double* dLdF) {
     if (op.kind == Op::UPDATE) ua = op.ua;
   AdjointArgs aa{};
   aa.dLdF = ctx->adj_gF;
-  aa.force = ctx->has_force ? ctx->dl[0].force : nullptr;
+  aa.force = !ctx->has_force ? nullptr
+             : ctx->storage == LBM_F64 ? static_cast<const void*>(ctx->dl[0].force)
+                                        : static_cast<const void*>(ctx->dl[0].force_f);
   aa.BX = lp.BX;
   aa.BY = lp.BY;
   aa.BZ = lp.BZ;

@@ -49,7 +49,8 @@ struct UpdateArgs {
   int nitems;
   const uint32_t* masks;  // 16 words per mask
   double cs2_18;          // 18 Cs^2
-  const double* force;    // level 0 body force [3][nblocks*512] (block order) or nullptr
+  const void* force;      // level 0 body force [3][nblocks*512] (block order) in the
+                          // compute type (double for F64 storage, else float) or nullptr
 };
 
 // coarse-to-fine work comes in chunks of consecutive ghost cells (sorted by
@@ -197,6 +198,8 @@ struct SlabArgs {
 };
 cudaError_t launch_slab(int model, int storage, const SlabArgs& a, cudaStream_t st);
 cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t st);
+// float copy of a float64 array (the compute-type body force of FP32/FP16 storage)
+cudaError_t launch_to_float(const double* in, float* out, long long n, cudaStream_t st);
 
 struct GatherArgs {
   const void* f;
@@ -214,7 +217,7 @@ struct AdjointArgs {
   const void* lam_in;   // lambda_{t+1}, same layout
   void* lam_out;        // lambda_t
   void* dLdF;           // [3][nblocks*512] accumulator (compute type)
-  const double* force;  // [3][nblocks*512] or nullptr
+  const void* force;    // [3][nblocks*512] in the compute type, or nullptr
   int BX, BY, BZ, nblocks;
   double omega;
 };

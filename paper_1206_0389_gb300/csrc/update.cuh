@@ -107,8 +107,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
         if (a.force != nullptr && w.level == 0) {
           const int64_t n = int64_t(L.BX) * L.BY * L.BZ * kCells;
           const int64_t j = int64_t(w.block) * kCells + c;
-          collide27_closed<T, true, kScaled>(g, T(1) / tau0, T(a.force[j]), T(a.force[n + j]),
-                                             T(a.force[2 * n + j]));
+          const T* F = reinterpret_cast<const T*>(a.force);
+          collide27_closed<T, true, kScaled>(g, T(1) / tau0, F[j], F[n + j], F[2 * n + j]);
         } else {
           collide27_closed<T, false, kScaled>(g, T(1) / tau0, T(0), T(0), T(0));
         }

@@ -220,6 +220,17 @@ __global__ void k_fill(double* p, long long n, double v) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) p[t] = v;
 }
+__global__ void k_to_float(const double* in, float* out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = float(in[i]);
+}
+
+cudaError_t launch_to_float(const double* in, float* out, long long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_to_float<<<unsigned((n + 255) / 256), 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   k_fill<<<unsigned((n + 255) / 256), 256, 0, st>>>(p, n, v);
