@@ -206,7 +206,7 @@ int lbm_get_profile(lbm_ctx* ctx, double ms[5], int64_t launches[5]);
 /* Launch configuration of the stream-collide kernel chosen by the autotuner:
  * threads per CTA, the minimum resident CTAs per SM the kernel was compiled
  * for (1 = no register cap), and CTAs per launch (0 = one CTA per block).
- * lbm_create times the shapes (128,1) (256,1) (128,8) (256,4), each
+ * lbm_create times the shapes (128,1) (256,1) (128,8) (256,4) (128,7), each
  * with one CTA per block and as a persistent grid, on the largest update
  * launch of the schedule.  Environment: LBM_AUTOTUNE=0 skips the timing and
  * keeps (256,1, one CTA per block); LBM_LAUNCH_SHAPE="threads,min,persistent"

@@ -394,7 +394,7 @@ int build_graphs(lbm_ctx* ctx) {
 }
 
 // Pick the stream-collide launch shape by timing the largest update launch of
-// the schedule: threads per CTA in {128, 256}, one CTA per block or a
+// the schedule: threads per CTA in {128, 256} with register caps, one CTA per block or a
 // persistent grid of (CTAs per SM x SMs).  Writes only the other buffer.
 int autotune(lbm_ctx* ctx) {
   const char* env = std::getenv("LBM_AUTOTUNE");
@@ -411,7 +411,7 @@ int autotune(lbm_ctx* ctx) {
   int bt = 256, bm = 1, bc = 0;
   // (no 512-thread shape: with one pass over the 512 cells of a block its
   // kernel is optimised into differently rounded arithmetic)
-  const int shapes[4][2] = {{128, 1}, {256, 1}, {128, 8}, {256, 4}};
+  const int shapes[5][2] = {{128, 1}, {256, 1}, {128, 8}, {256, 4}, {128, 7}};
   // LBM_LAUNCH_SHAPE="threads,min_ctas_per_sm,persistent" fixes one of the
   // shapes below without timing (profilers distort the timings).
   if (const char* fixed = std::getenv("LBM_LAUNCH_SHAPE")) {

@@ -167,7 +167,8 @@ template <class M, class S>
 cudaError_t launch_ms(const UpdateArgs& a, int threads, int minb, int ctas, cudaStream_t st) {
   if (a.nitems == 0) return cudaSuccess;
   const int grid = ctas > 0 ? std::min(ctas, a.nitems) : a.nitems;
-  if (threads == 128 && minb == 1) k_update<M, S, 128, 1><<<grid, 128, 0, st>>>(a);
+  if (threads == 128 && minb == 7) k_update<M, S, 128, 7><<<grid, 128, 0, st>>>(a);
+  else if (threads == 128 && minb == 1) k_update<M, S, 128, 1><<<grid, 128, 0, st>>>(a);
   else if (threads == 256 && minb == 1) k_update<M, S, 256, 1><<<grid, 256, 0, st>>>(a);
   else if (threads == 128 && minb == 8) k_update<M, S, 128, 8><<<grid, 128, 0, st>>>(a);
   else if (threads == 256 && minb == 4) k_update<M, S, 256, 4><<<grid, 256, 0, st>>>(a);
@@ -177,6 +178,7 @@ cudaError_t launch_ms(const UpdateArgs& a, int threads, int minb, int ctas, cuda
 
 template <class M, class S>
 cudaError_t occ_ms(int threads, int minb, int* n) {
+  if (threads == 128 && minb == 7) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 7>, 128, 0);
   if (threads == 128 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 1>, 128, 0);
   if (threads == 256 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 256, 1>, 256, 0);
   if (threads == 128 && minb == 8) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 8>, 128, 0);

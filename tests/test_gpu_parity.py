@@ -36,7 +36,7 @@ def close(ctx):
 
 # every compiled stream-collide variant: no register cap, 64-register cap
 # (one CTA per block and persistent)
-VARIANTS = ["128,1,0", "128,8,0", "256,4,1"]
+VARIANTS = ["128,1,0", "128,8,0", "256,4,1", "128,7,0"]
 
 
 @pytest.mark.parametrize("model", MODELS)
@@ -461,7 +461,7 @@ def valid_cells(lbm, ctx, l):
 # register cap of min CTAs per SM): within a group only the thread count and
 # the grid differ
 SHAPE_GROUPS = [["128,1,0", "256,1,0", "128,1,1", "256,1,1"],
-                ["128,8,0", "128,8,1"], ["256,4,0", "256,4,1"]]
+                ["128,8,0", "128,8,1"], ["256,4,0", "256,4,1"], ["128,7,0", "128,7,1"]]
 
 
 def run_with_shape(lbm, monkeypatch, sh, model, storage, steps=4):
