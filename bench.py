@@ -272,7 +272,23 @@ def run_jet3(lbm, torch, storage, steps, warmup, stream):
     lbm.lbm_set_profiling(ctx, True)
     lbm.lbm_step(ctx, 2)
     pms, pn = lbm.lbm_get_profile(ctx)
+    lbm.lbm_set_profiling(ctx, False)
     m = lbm.lbm_mass_momentum(ctx)
+    # time-averaged centreline velocity over the next 50 coarse steps (not
+    # timed; the paper's evaluation quantity, reported, not gated): the axis
+    # lies on level 0 (the refined rings start at r = 8)
+    lbm.lbm_stats_reset(ctx)
+    for _ in range(50):
+        lbm.lbm_step(ctx, 1)
+        lbm.lbm_stats_accumulate(ctx)
+    mean, var, nsamp = lbm.lbm_stats_get(ctx, 0)
+    jy, jz = int(centre[0]) - 1, int(centre[1]) - 1
+    axis_ux = mean[1, jz:jz + 2, jy:jy + 2, :].mean(axis=(0, 1))
+    axis_var = var[0, jz:jz + 2, jy:jy + 2, :].mean(axis=(0, 1))
+    centreline = {"%g" % xd: round(float(axis_ux[int(xd * 32)]) / 0.05, 5) for xd in (0, 0.25, 0.5, 1, 2)}
+    intensity = {"%g" % xd: round(float(np.sqrt(max(axis_var[int(xd * 32)], 0.0))) / 0.05, 5)
+                 for xd in (0, 0.25, 0.5)}
+    total_steps = warmup + steps + 2 + 50
     lbm.lbm_destroy(ctx)
     upd = info.active_updates_per_coarse_step
     peak, _ = measured_peak()
@@ -283,7 +299,11 @@ def run_jet3(lbm, torch, storage, steps, warmup, stream):
             "frac_of_hbm_roofline": round(bpu * upd / (ms * 1e-3) / 1e9 / peak, 4),
             "profile_ms_per_coarse_step": {k: round(float(v) / 2, 4) for k, v in
                                            zip(["update", "c2f", "f2c", "bc", "other"], pms)},
-            "launches_per_coarse_step": int(pn.sum()) // 2, "final_momentum_x": float(m[1])}
+            "launches_per_coarse_step": int(pn.sum()) // 2, "final_momentum_x": float(m[1]),
+            "centreline_mean_ux_over_u_in_by_x_over_D": centreline,
+            "centreline_rms_ux_over_u_in_by_x_over_D": intensity,
+            "statistics_window": "coarse steps %d-%d after start from rest (%d samples)" % (
+                total_steps - 50 + 1, total_steps, nsamp)}
 
 
 def run_adjoint(lbm, torch, stream, T=256, every=16, N=96):

@@ -135,6 +135,20 @@ int lbm_sync(lbm_ctx* ctx);
  * of the level (unrefined cells and hidden layers); NaN elsewhere. */
 int lbm_macroscopic(lbm_ctx* ctx, int level, double* rho, double* u);
 
+/* Time statistics of the flow (the paper's jet evaluation quantities are
+ * time averages: mean velocity along the centreline, spreading, turbulence
+ * intensity, Section 3.3).  lbm_stats_reset allocates (first call) and zeroes
+ * float64 sums of rho, u and u_a^2 per cell of every level (56 bytes per
+ * allocated cell); lbm_stats_accumulate adds one sample of the current state
+ * of every level (enqueued, no synchronisation); lbm_stats_get returns, for
+ * one level, the means mean[4][NZ][NY][NX] = (rho, u_x, u_y, u_z) and the
+ * variances var[3][NZ][NY][NX] = <u_a^2> - <u_a>^2 over the samples, NaN where
+ * a cell holds no value of the level, and the sample count.  u is taken as in
+ * lbm_macroscopic without a body force.  LBM_ERR_STATE before any sample. */
+int lbm_stats_reset(lbm_ctx* ctx);
+int lbm_stats_accumulate(lbm_ctx* ctx);
+int lbm_stats_get(lbm_ctx* ctx, int level, double* mean, double* var, int64_t* nsamples);
+
 /* Float64 sums over the unrefined cells of all levels, weighted by the cell
  * volume 8^-l: out = {sum (rho - 1), sum j_x, sum j_y, sum j_z}, j = sum f e.
  * LBM_ERR_NONFINITE if any summed value is NaN/Inf. */

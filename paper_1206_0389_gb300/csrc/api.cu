@@ -49,6 +49,7 @@ struct DevLevel {
   BCItem* bc = nullptr;
   double* force = nullptr;
   float* force_f = nullptr;  // float copy for FP32/FP16 storage (compute type)
+  double* stats = nullptr;   // time statistics sums [7][nblocks*512]
 };
 
 }  // namespace
@@ -78,6 +79,7 @@ struct lbm_ctx {
   int64_t step = 0;
   bool need_restrict = false;
   bool has_force = false;
+  long long stats_n = 0;  // samples in the statistics sums
   // inflow
   double y0 = 0, z0 = 0, diameter = 0, u_in = 0, perturb = 0;
   uint64_t seed = 0;
@@ -142,6 +144,7 @@ void free_all(lbm_ctx* c) {
     cudaFree(d.bc);
     cudaFree(d.force);
     cudaFree(d.force_f);
+    cudaFree(d.stats);
   }
   cudaFree(c->items);
   cudaFree(c->masks);
@@ -481,7 +484,7 @@ int cur_parity(const lbm_ctx* ctx, int level) { return level == 0 ? ctx->parity0
 // hout[c] are the host arrays of the comps components ([NZ][NY][NX] each);
 // a NULL input component is filled with fill[c] on the device.
 int slab_transfer(lbm_ctx* ctx, int level, int mode, const double* const* hin, double* const* hout,
-                  int comps, const double* fill = nullptr, void* raw = nullptr) {
+                  int comps, const double* fill = nullptr, void* raw = nullptr, double scale = 1.0) {
   const LevelPlan& lp = ctx->plan.lv[level];
   const int64_t plane = int64_t(lp.NX) * lp.NY;
   int nz = 8;
@@ -519,6 +522,7 @@ int slab_transfer(lbm_ctx* ctx, int level, int mode, const double* const* hin, d
     a.out = ctx->stage;
     a.mode = mode;
     a.raw = raw;
+    a.scale = scale;
     CK(launch_slab(ctx->model, ctx->storage, a, ctx->stream));
     if (hout)
       for (int c = 0; c < comps; ++c)
@@ -831,6 +835,47 @@ int lbm_macroscopic(lbm_ctx* ctx, int level, double* rho, double* u) {
   const size_t n = size_t(lp.NX) * lp.NY * lp.NZ;
   double* hout[4] = {rho, u, u + n, u + 2 * n};
   return slab_transfer(ctx, level, SLAB_MACRO, nullptr, hout, 4);
+}
+
+int lbm_stats_reset(lbm_ctx* ctx) {
+  if (!ctx) return LBM_ERR_ARG;
+  for (int l = 0; l < ctx->L; ++l) {
+    const size_t bytes = size_t(ctx->plan.lv[l].nblocks()) * 512 * 7 * sizeof(double);
+    if (!ctx->dl[l].stats) {
+      cudaError_t e = cudaMalloc(&ctx->dl[l].stats, bytes);
+      if (e != cudaSuccess) return fail(ctx, LBM_ERR_OOM, std::string("statistics: ") + cudaGetErrorString(e));
+    }
+    CK(cudaMemsetAsync(ctx->dl[l].stats, 0, bytes, ctx->stream));
+  }
+  ctx->stats_n = 0;
+  return LBM_OK;
+}
+
+int lbm_stats_accumulate(lbm_ctx* ctx) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (!ctx->dl[0].stats) return fail(ctx, LBM_ERR_STATE, "call lbm_stats_reset first");
+  for (int l = 0; l < ctx->L; ++l) {
+    StatsArgs a{};
+    a.f = ctx->dl[l].f[cur_parity(ctx, l)];
+    a.kind = ctx->dl[l].kind;
+    a.ncells = ctx->plan.lv[l].nblocks() * 512;
+    a.sums = ctx->dl[l].stats;
+    CK(launch_stats(ctx->model, ctx->storage, a, ctx->stream));
+  }
+  ctx->stats_n++;
+  return LBM_OK;
+}
+
+int lbm_stats_get(lbm_ctx* ctx, int level, double* mean, double* var, int64_t* nsamples) {
+  if (!ctx || !mean || !var) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+  if (level < 0 || level >= ctx->L) return fail(ctx, LBM_ERR_ARG, "level out of range");
+  if (!ctx->dl[0].stats || ctx->stats_n == 0) return fail(ctx, LBM_ERR_STATE, "no samples accumulated");
+  const LevelPlan& lp = ctx->plan.lv[level];
+  const size_t n = size_t(lp.NX) * lp.NY * lp.NZ;
+  double* hout[7] = {mean, mean + n, mean + 2 * n, mean + 3 * n, var, var + n, var + 2 * n};
+  if (nsamples) *nsamples = ctx->stats_n;
+  return slab_transfer(ctx, level, SLAB_GET_STATS, nullptr, hout, 7, nullptr, ctx->dl[level].stats,
+                       1.0 / double(ctx->stats_n));
 }
 
 int lbm_mass_momentum(lbm_ctx* ctx, double out[4]) {

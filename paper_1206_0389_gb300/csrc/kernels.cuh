@@ -184,7 +184,7 @@ cudaError_t launch_step_inc(long long* step, cudaStream_t st);
 // dense <-> block staging for one slab of cell layers [z0, z0 + nz) of a level
 enum SlabMode { SLAB_SET_STATE = 0, SLAB_GET_STATE = 1, SLAB_INIT_EQ = 2, SLAB_MACRO = 3,
                 SLAB_SET_FORCE = 4, SLAB_SET_LAMBDA = 5, SLAB_GET_FIELD3 = 6, SLAB_GET_AUX = 7,
-                SLAB_SET_AUX = 8 };
+                SLAB_SET_AUX = 8, SLAB_GET_STATS = 9 };
 struct SlabArgs {
   void* f;                // level storage (current buffer)
   const uint8_t* kind;    // [nblocks][512] cell kinds
@@ -194,8 +194,20 @@ struct SlabArgs {
   const double* in;       // SET_STATE: f [Q][n]; INIT_EQ: rho [n], u [3][n]; SET_FORCE: F [3][n]
   double* out;            // GET_STATE: f [Q][n]; MACRO: rho [n], u [3][n]
   int mode;
-  void* raw;              // SET_LAMBDA: [block][Q][512] (compute type); GET_FIELD3: [3][nblocks*512]
+  void* raw;              // SET_LAMBDA: [block][Q][512] (compute type); GET_FIELD3: [3][nblocks*512];
+                          // GET_STATS: the statistics sums [7][nblocks*512] (double)
+  double scale;           // GET_STATS: 1 / number of samples
 };
+
+// time statistics of a level: sums over samples of rho, u_x, u_y, u_z,
+// u_x^2, u_y^2, u_z^2 per cell ([7][nblocks*512], block order, float64)
+struct StatsArgs {
+  const void* f;
+  const uint8_t* kind;
+  long long ncells;  // nblocks * 512
+  double* sums;
+};
+cudaError_t launch_stats(int model, int storage, const StatsArgs& a, cudaStream_t st);
 cudaError_t launch_slab(int model, int storage, const SlabArgs& a, cudaStream_t st);
 cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t st);
 // float copy of a float64 array (the compute-type body force of FP32/FP16 storage)

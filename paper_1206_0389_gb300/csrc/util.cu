@@ -104,6 +104,19 @@ __global__ void k_slab(const SlabArgs a) {
       for (int c = 0; c < 3; ++c) a.out[c * n + t] = j < 0 ? nan : double(r[c * nn + j]);
       return;
     }
+    case SLAB_GET_STATS: {
+      // mean rho, u_x, u_y, u_z, then the variances <u_a^2> - <u_a>^2
+      const uint8_t k = j < 0 ? uint8_t(K_NONE) : a.kind[j];
+      const bool ok = k == K_ACTIVE || k == K_HIDDEN1 || k == K_HIDDEN2;
+      const int64_t nn = int64_t(a.BX) * a.BY * a.BZ * kCells;
+      const double* r = reinterpret_cast<const double*>(a.raw);
+      for (int c = 0; c < 4; ++c) a.out[c * n + t] = ok ? r[c * nn + j] * a.scale : nan;
+      for (int c = 0; c < 3; ++c) {
+        const double m = ok ? r[(1 + c) * nn + j] * a.scale : 0.0;
+        a.out[(4 + c) * n + t] = ok ? r[(4 + c) * nn + j] * a.scale - m * m : nan;
+      }
+      return;
+    }
     case SLAB_GET_AUX: {
       a.out[t] = j < 0 ? nan : double(reinterpret_cast<const T*>(a.raw)[j]);
       return;
@@ -220,6 +233,55 @@ __global__ void k_fill(double* p, long long n, double v) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) p[t] = v;
 }
+// one sample of the time statistics: rho and u of every cell holding a value
+// of the level (the same moments as the macroscopic output), accumulated in
+// float64
+template <class M, class S>
+__global__ void k_stats(const StatsArgs a) {
+  constexpr int Q = M::Q;
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= a.ncells) return;
+  const uint8_t k = a.kind[j];
+  if (k != K_ACTIVE && k != K_HIDDEN1 && k != K_HIDDEN2) return;
+  const S* f = reinterpret_cast<const S*>(a.f) + (j / kCells) * Q * kCells + (j % kCells);
+  double g[Q];
+  for (int i = 0; i < Q; ++i) g[i] = double(load_rt<S, Q>(f + i * kCells, i));
+  double rl = 0, jx = 0, jy = 0, jz = 0;
+  static_for<Q>([&](auto i) {
+    rl += g[i];
+    jx += Lattice<Q>::ex(i) * g[i];
+    jy += Lattice<Q>::ey(i) * g[i];
+    jz += Lattice<Q>::ez(i) * g[i];
+  });
+  const double rho = 1.0 + rl;
+  double ux = jx, uy = jy, uz = jz;
+  if (Q == 27) {
+    ux = jx / rho;
+    uy = jy / rho;
+    uz = jz / rho;
+  }
+  const double v[7] = {rho, ux, uy, uz, ux * ux, uy * uy, uz * uz};
+  for (int c = 0; c < 7; ++c) a.sums[c * a.ncells + j] += v[c];
+}
+
+template <class M, class S>
+static cudaError_t stats_ms(const StatsArgs& a, cudaStream_t st) {
+  if (a.ncells == 0) return cudaSuccess;
+  k_stats<M, S><<<unsigned((a.ncells + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats(int model, int storage, const StatsArgs& a, cudaStream_t st) {
+  if (model == LBM_D3Q19_MRT_LES) {
+    if (storage == LBM_F64) return stats_ms<MrtLes, double>(a, st);
+    if (storage == LBM_F32) return stats_ms<MrtLes, float>(a, st);
+    return stats_ms<MrtLes, __half>(a, st);
+  }
+  if (storage == LBM_F64) return stats_ms<Fclb, double>(a, st);
+  if (storage == LBM_F32) return stats_ms<Fclb, float>(a, st);
+  return stats_ms<Fclb, __half>(a, st);
+}
+
 __global__ void k_to_float(const double* in, float* out, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = float(in[i]);

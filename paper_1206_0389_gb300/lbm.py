@@ -25,7 +25,7 @@ EXPORTED = ["lbm_plan", "lbm_create", "lbm_create_error", "lbm_set_inflow", "lbm
             "lbm_set_profiling", "lbm_get_profile", "lbm_get_tuning", "lbm_last_error", "lbm_destroy",
             "lbm_mass_momentum_noalloc", "lbm_adjoint_forward", "lbm_adjoint_backward",
             "lbm_get_strain", "lbm_set_strain", "lbm_raw_state_bytes", "lbm_get_raw_state",
-            "lbm_set_raw_state"]
+            "lbm_set_raw_state", "lbm_stats_reset", "lbm_stats_accumulate", "lbm_stats_get"]
 NOALLOC_MAX_BLOCKS = 65536
 
 
@@ -76,6 +76,9 @@ def load():
         "lbm_get_cells": (c_int, [c_void_p, c_int, c_size_t, P(c_int64), D]),
         "lbm_get_strain": (c_int, [c_void_p, c_int, D, c_size_t]),
         "lbm_raw_state_bytes": (c_int, [c_void_p, c_int, P(c_size_t)]),
+        "lbm_stats_reset": (c_int, [c_void_p]),
+        "lbm_stats_accumulate": (c_int, [c_void_p]),
+        "lbm_stats_get": (c_int, [c_void_p, c_int, D, D, P(c_int64)]),
         "lbm_get_raw_state": (c_int, [c_void_p, c_int, c_void_p, c_size_t]),
         "lbm_set_raw_state": (c_int, [c_void_p, c_int, c_void_p, c_size_t]),
         "lbm_set_strain": (c_int, [c_void_p, c_int, D, c_size_t]),
@@ -214,6 +217,25 @@ def lbm_get_state(ctx, level):
 def lbm_set_state(ctx, level, f):
     a = _f64(f)
     _check(ctx, load().lbm_set_state(ctx.h, level, _dptr(a), a.size))
+
+
+def lbm_stats_reset(ctx):
+    _check(ctx, load().lbm_stats_reset(ctx.h))
+
+
+def lbm_stats_accumulate(ctx):
+    _check(ctx, load().lbm_stats_accumulate(ctx.h))
+
+
+def lbm_stats_get(ctx, level):
+    """(mean [4, NZ, NY, NX] of rho, u_x, u_y, u_z; variance [3, NZ, NY, NX]
+    of u; number of samples) of the accumulated time statistics."""
+    NX, NY, NZ = ctx.dims(level)
+    mean = np.empty((4, NZ, NY, NX))
+    var = np.empty((3, NZ, NY, NX))
+    n = c_int64()
+    _check(ctx, load().lbm_stats_get(ctx.h, level, _dptr(mean), _dptr(var), ctypes.byref(n)))
+    return mean, var, n.value
 
 
 def lbm_raw_state_bytes(ctx, level):

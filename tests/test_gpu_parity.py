@@ -281,6 +281,65 @@ def test_nested_parity_refined_patch_on_inflow_face(model):
 
 
 @pytest.mark.parametrize("model", MODELS)
+def test_time_statistics_match_oracle(model):
+    """Time-averaged rho, u and the velocity variances over three coarse steps
+    of a nested run with inflow, against the same averages of the oracle's
+    macroscopic fields (float64)."""
+    lbm = gpu()
+    nb, ref = jet_grid(2)
+    ctx, orc = make_pair(model, "f64", nb, False, ref, omega=1.7, cs=0.18)
+    init_both(ctx, orc, nested_fields(orc))
+    lbm.lbm_set_inflow(ctx, 8.0, 8.0, 8.0, 0.05, 0.01, 4321)
+    orc.set_inflow(8.0, 8.0, 8.0, 0.05, 0.01, 4321)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_stats_accumulate(ctx)
+    lbm.lbm_stats_reset(ctx)
+    acc = [None, None]
+    for _ in range(3):
+        lbm.lbm_step(ctx, 1)
+        orc.step(1)
+        lbm.lbm_stats_accumulate(ctx)
+        for l in range(2):
+            ro, uo = orc.macroscopic(l)
+            ro, uo = ro.numpy(), uo.numpy()
+            v = np.concatenate([ro[None], uo, uo * uo])
+            acc[l] = v if acc[l] is None else acc[l] + v
+    for l in range(2):
+        mean, var, n = lbm.lbm_stats_get(ctx, l)
+        assert n == 3
+        mo = acc[l][:4] / 3
+        vo = acc[l][4:] / 3 - mo[1:] ** 2
+        assert np.array_equal(np.isnan(mean), np.isnan(mo))
+        ok = ~np.isnan(mo[0])
+        assert np.abs(mean[:, ok] - mo[:, ok]).max() <= 1e-12
+        assert np.abs(var[:, ok] - vo[:, ok]).max() <= 1e-12
+        assert var[:, ok].max() > 0
+    close(ctx)
+
+
+def test_coarsened_paper_jet_parity_f64():
+    """The paper-scale 3-level jet's layout on a 4x-coarsened domain (coarse
+    128 x 64 x 64, nozzle D = 8, level 1 within 12 coarse cells of the axis
+    over x < 48, level 2 within 8 over x < 24), D3Q27 FCLB in float64 with
+    inflow and outflow: one coarse step (every level's substeps, both
+    interfaces of both level pairs) against the oracle."""
+    lbm = gpu()
+    nb = (16, 8, 8)
+    flags, centre = synth.jet_three_level(*nb, r1=(0.0, 12.0), r2=(0.0, 8.0), x1=(0, 48), x2=(0, 24))
+    nu_c = 0.05 * 8 / 1e4
+    omega = 1.0 / (3 * nu_c + 0.5)
+    ctx, orc = make_pair("d3q27", "f64", nb, False, flags, omega=omega, cs=0.0)
+    assert len(orc.levels) == 3
+    lbm.lbm_set_inflow(ctx, centre[0], centre[1], 8.0, 0.05, 0.01, 5120)
+    orc.set_inflow(centre[0], centre[1], 8.0, 0.05, 0.01, 5120)
+    lbm.lbm_step(ctx, 1)
+    orc.step(1)
+    d, s = compare_levels(ctx, orc)
+    assert d <= 1e-12, d
+    close(ctx)
+
+
+@pytest.mark.parametrize("model", MODELS)
 def test_nested_parity_f32_per_step(model):
     lbm = gpu()
     nb, ref = jet_grid(2)
