@@ -37,7 +37,17 @@ library's documented setup): x may be periodic; otherwise the ghost column
 x = -1 holds f_eq(rho of the cell x = 0, u_bc) with the top-hat disc
 velocity u_bc = u_in (1 + p xi_x, p xi_y, p xi_z) inside r < D/2 and 0
 outside, and the ghost column x = NX holds a copy of cell x = NX - 1
-(zero-gradient outflow).  y and z are periodic.
+(zero-gradient outflow).  y and z are periodic unless walls are requested.
+
+Walls (Section 3.2 names no-slip walls for the tank and a free-slip top):
+both faces of y and/or z may be walls of level 0 (refined blocks keep one
+block away from them).  A population whose pull would cross a wall face is
+reflected: at a no-slip face by half-way bounce-back, f_i(x, t+1) =
+f~_opp(i)(x, t) (the wall lies half a cell outside the boundary cells); at a
+free-slip face by specular reflection, the population with the wall-normal
+velocity component flipped, pulled from the same layer, f_i(x, t+1) =
+f~_m(i)(x - e_i + (e_i . n) n, t).  Where a link crosses two walls, a no-slip
+crossing wins; two free-slip crossings reflect both components.
 """
 import math
 
@@ -51,10 +61,26 @@ from .rng import inflow_xi
 
 
 class NestedSolver:
-    def __init__(self, model, nb, periodic_x=True, refine=(), omega=1.0, cs=0.0):
+    def __init__(self, model, nb, periodic_x=True, refine=(), omega=1.0, cs=0.0, walls=0, slip=0):
+        """walls: bit 0/1 the low/high y face, bit 2/3 the low/high z face are
+        walls (both faces of an axis or neither); slip: the same bits mark the
+        free-slip walls among them (the others are no-slip)."""
         self.m = Model(model)
         self.Q = self.m.Q
-        self.levels = build_levels(nb, periodic_x, list(refine))
+        if (walls & 3) not in (0, 3) or (walls & 12) not in (0, 12) or (slip & ~walls):
+            raise ValueError("walls come in pairs per axis; slip marks a subset of them")
+        self.walls, self.slip = int(walls), int(slip)
+        refine = list(refine)
+        if walls and refine:
+            r0 = refine[0].bool()
+            near = torch.zeros_like(r0)
+            if walls & 3:
+                near[:, 0, :] = near[:, -1, :] = True
+            if walls & 12:
+                near[0] = near[-1] = True
+            if bool((r0 & near).any()):
+                raise ValueError("refined blocks must keep one block away from the walls")
+        self.levels = build_levels(nb, periodic_x, refine)
         self.L = len(self.levels)
         self.periodic_x = periodic_x
         self.omega0 = float(omega)
@@ -146,6 +172,45 @@ class NestedSolver:
         if len(zz):
             f[:, zz, yy, lv.NX + 1] = f[:, zz, yy, lv.NX]
 
+    def _vel_index(self, ex, ey, ez):
+        for q in range(self.Q):
+            if tuple(int(v) for v in self.m.e[q]) == (ex, ey, ez):
+                return q
+        raise KeyError((ex, ey, ez))
+
+    def _wall_pulls(self, f, pre):
+        """Replace the pulls that cross a wall face of level 0 (see the
+        module docstring)."""
+        NZ, NY = f.shape[1], f.shape[2]
+        zz = torch.arange(NZ).reshape(NZ, 1, 1)
+        yy = torch.arange(NY).reshape(1, NY, 1)
+        W, S = self.walls, self.slip
+        for q in range(self.Q):
+            ex, ey, ez = (int(v) for v in self.m.e[q])
+            cy = torch.zeros((1, NY, 1), dtype=torch.bool)
+            cz = torch.zeros((NZ, 1, 1), dtype=torch.bool)
+            slip_y = slip_z = False
+            if ey == 1 and W & 1:
+                cy, slip_y = yy == 0, bool(S & 1)
+            if ey == -1 and W & 2:
+                cy, slip_y = yy == NY - 1, bool(S & 2)
+            if ez == 1 and W & 4:
+                cz, slip_z = zz == 0, bool(S & 4)
+            if ez == -1 and W & 8:
+                cz, slip_z = zz == NZ - 1, bool(S & 8)
+            cross = (cy | cz).expand(pre[q].shape)
+            if not bool(cross.any()):
+                continue
+            noslip = ((cy & (not slip_y)) | (cz & (not slip_z))).expand(pre[q].shape)
+            both = (cy & cz).expand(pre[q].shape)
+            only_y = (cy & ~cz).expand(pre[q].shape)
+            bounce = f[self._vel_index(-ex, -ey, -ez)]
+            mir_y = torch.roll(f[self._vel_index(ex, -ey, ez)], shifts=(ez, 0, ex), dims=(0, 1, 2))
+            mir_z = torch.roll(f[self._vel_index(ex, ey, -ez)], shifts=(0, ey, ex), dims=(0, 1, 2))
+            mir_yz = torch.roll(f[self._vel_index(ex, -ey, -ez)], shifts=(0, 0, ex), dims=(0, 1, 2))
+            mirrored = torch.where(both, mir_yz, torch.where(only_y, mir_y, mir_z))
+            pre[q] = torch.where(cross, torch.where(noslip, bounce, mirrored), pre[q])
+
     def _update(self, l):
         """Pull streaming and collision on the update mask of level l."""
         lv = self.levels[l]
@@ -154,6 +219,8 @@ class NestedSolver:
         for q in range(self.Q):
             ex, ey, ez = (int(v) for v in self.m.e[q])
             pre[q] = torch.roll(f[q], shifts=(ez, ey, ex), dims=(0, 1, 2))
+        if l == 0 and self.walls:
+            self._wall_pulls(f, pre)
         mask = lv.update
         fin = pre[:, mask]
         force = None

@@ -123,3 +123,42 @@ def test_wrong_inflow_velocity_is_caught(monkeypatch):
         return orig(self, l, sub)
     monkeypatch.setattr(S.NestedSolver, "_apply_bc", bc)
     assert fails(TN.test_inflow_ghosts_carry_disc_velocity, "d3q19")
+
+
+def test_bounce_back_without_reversal_is_caught(monkeypatch):
+    """A no-slip wall that returns the incoming population itself instead of
+    its opposite (no momentum reversal)."""
+    from tests import test_oracle_walls as TW
+    orig = S.NestedSolver._vel_index
+
+    def idx(self, ex, ey, ez):
+        return orig(self, -ex, -ey, -ez) if (ex, ey, ez) != (0, 0, 0) else orig(self, 0, 0, 0)
+
+    def wall_pulls(self, f, pre):
+        # bounce-back reads f_i instead of f_opp(i): flip the lookup only there
+        monkeypatch.setattr(S.NestedSolver, "_vel_index", idx)
+        try:
+            S_orig_wall(self, f, pre)
+        finally:
+            monkeypatch.setattr(S.NestedSolver, "_vel_index", orig)
+    S_orig_wall = S.NestedSolver._wall_pulls
+    monkeypatch.setattr(S.NestedSolver, "_wall_pulls", wall_pulls)
+    assert fails(TW.test_no_slip_poiseuille_profile)
+
+
+def test_free_slip_flipping_the_tangential_component_is_caught(monkeypatch):
+    """A free-slip wall that mirrors the wrong velocity component."""
+    from tests import test_oracle_walls as TW
+    orig = S.NestedSolver._vel_index
+
+    def wall_pulls(self, f, pre):
+        def idx(s, ex, ey, ez):
+            return orig(s, -ex, ey, ez) if ex != 0 else orig(s, ex, ey, ez)
+        monkeypatch.setattr(S.NestedSolver, "_vel_index", idx)
+        try:
+            orig_wall(self, f, pre)
+        finally:
+            monkeypatch.setattr(S.NestedSolver, "_vel_index", orig)
+    orig_wall = S.NestedSolver._wall_pulls
+    monkeypatch.setattr(S.NestedSolver, "_wall_pulls", wall_pulls)
+    assert fails(TW.test_free_slip_keeps_tangential_uniform_flow, "d3q27")

@@ -1,0 +1,80 @@
+"""Pins of the oracle's wall reflections (no-slip half-way bounce-back and
+free-slip specular reflection on the y / z faces; Section 3.2 names no-slip
+tank walls and a free-slip top)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import DTYPE
+from oracle.solver import NestedSolver
+from tests.helpers import random_state
+
+MODELS = ["d3q19", "d3q27"]
+
+
+def solver(model, nb, walls, slip, omega=1.6, **kw):
+    return NestedSolver(model, nb, periodic_x=True, omega=omega, cs=0.1 if model == "d3q19" else 0.0,
+                        walls=walls, slip=slip, **kw)
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("walls,slip", [(3, 0), (15, 12), (15, 2), (12, 12)])
+def test_walls_conserve_mass(model, walls, slip):
+    """Reflections only move populations: the total mass of a far-from-
+    equilibrium state is conserved to round-off (the D3Q19 model stores
+    the fluctuation, so its sum is the mass deviation)."""
+    s = solver(model, (1, 2, 2), walls, slip)
+    lv = s.levels[0]
+    f = torch.from_numpy(random_state(model, (lv.NX, lv.NY, lv.NZ), 7, 0.2))
+    s.set_state(0, f)
+    m0 = s.state(0).sum().item()
+    s.step(5)
+    assert abs(s.state(0).sum().item() - m0) <= 1e-12 * f.numel()
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_free_slip_keeps_tangential_uniform_flow(model):
+    """A uniform flow tangential to free-slip walls (both y and z faces) is an
+    exact steady state: the mirrored equilibrium population is the same
+    equilibrium value."""
+    s = solver(model, (1, 1, 2), 15, 15)
+    lv = s.levels[0]
+    u = torch.zeros(3, lv.NZ, lv.NY, lv.NX, dtype=DTYPE)
+    u[0] = 0.05
+    s.init_equilibrium(0, None, u)
+    f0 = s.state(0)
+    s.step(5)
+    assert (s.state(0) - f0).abs().max().item() <= 1e-14
+
+
+def test_no_slip_poiseuille_profile():
+    """Body-force-driven channel between no-slip y walls (half-way
+    bounce-back puts them half a cell outside the boundary cells): the
+    parabola u_x(y) = F / (2 nu) (y + 1/2) (H - 1/2 - y) is kept within 1 % of
+    its maximum over 200 steps (D3Q27 FCLB, tau = 0.8)."""
+    NY, tau, umax = 16, 0.8, 0.01
+    nu = (tau - 0.5) / 3
+    F = 8 * nu * umax / NY ** 2
+    s = solver("d3q27", (1, 2, 1), 3, 0, omega=1 / tau)
+    lv = s.levels[0]
+    y = torch.arange(NY, dtype=DTYPE)
+    ux = F / (2 * nu) * (y + 0.5) * (NY - 0.5 - y)
+    u = torch.zeros(3, lv.NZ, lv.NY, lv.NX, dtype=DTYPE)
+    u[0] = ux[None, :, None]
+    s.init_equilibrium(0, None, u)
+    Fv = torch.zeros(3, lv.NZ, lv.NY, lv.NX, dtype=DTYPE)
+    Fv[0] = F
+    s.set_force(Fv)
+    s.step(200)
+    _, uu = s.macroscopic(0)
+    assert (uu[0] - ux[None, :, None]).abs().max().item() <= 0.01 * umax
+    assert uu[1].abs().max().item() <= 1e-6 * umax
+
+
+def test_walls_reject_refinement_next_to_them():
+    r = torch.zeros(2, 2, 2, dtype=torch.bool)
+    r[0, 0, 0] = True
+    with pytest.raises(ValueError):
+        NestedSolver("d3q27", (2, 2, 2), refine=[r], walls=3)
+    with pytest.raises(ValueError):
+        NestedSolver("d3q27", (2, 2, 2), walls=1)
