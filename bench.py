@@ -218,14 +218,16 @@ def velocity_error(lbm, ctx, ref_u):
     return float(np.sqrt(((u - ref_u) ** 2).sum() / (ref_u ** 2).sum()))
 
 
-def run_jet(lbm, torch, model, steps, warmup, stream):
+def run_jet(lbm, torch, model, steps, warmup, stream, walls=0, slip=0):
+    """2-level jet (coarse 384x192x192, fine cylinder of radius 24 coarse
+    cells); walls/slip put it in a tank (y/z wall faces, free-slip subset)."""
     import synth
     flags, centre = synth.jet_two_level()
     nu_c = 0.05 * 16 / 1e4
     ctx = lbm.lbm_create(model, "f32", (48, 24, 24), False, flags, 1.0 / (3 * nu_c + 0.5),
-                         0.18 if model == "d3q19" else 0.0, stream.cuda_stream)
+                         0.18 if model == "d3q19" else 0.0, stream.cuda_stream, walls=walls, slip=slip)
     lbm.lbm_set_inflow(ctx, centre[0], centre[1], 16.0, 0.05, 0.01, 389)
-    info = lbm.lbm_plan((48, 24, 24), False, flags, model, "f32")
+    info = lbm.lbm_plan((48, 24, 24), False, flags, model, "f32", walls=walls, slip=slip)
     lbm.lbm_step(ctx, warmup)
     lbm.lbm_sync(ctx)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -385,14 +387,16 @@ def ours(args):
     field = synth.spectrum_field(N_GRID, seed=1206 + rank)
     K, W = args.steps, args.warmup
 
-    if args.kernel_only and args.variant.startswith(("jet2s_", "jet3s_", "jet3p_")):
+    if args.kernel_only and args.variant.startswith(("jet2s_", "jet2t_", "jet3s_", "jet3p_")):
         # jets for profiling the interface and boundary kernels:
         # jet2s = 2 levels (coarse 192x96x96, fine cylinder of radius 12);
+        # jet2t = jet2s in a tank (no-slip sides and bottom, free-slip top);
         # jet3s = the 3-level jet at half the paper's scale (coarse
         # 256x128x128, D = 16, 1.8 GB in FP32); jet3p = the paper-scale
         # 3-level jet (11.3 GB in FP32: launch lists only, no full captures)
         kind, model, storage = args.variant.split("_")
-        if kind == "jet2s":
+        walls, slip = (15, 8) if kind == "jet2t" else (0, 0)
+        if kind in ("jet2s", "jet2t"):
             nb, D = (24, 12, 12), 8.0
             flags, centre = synth.jet_two_level(*nb, radius=12.0)
         elif kind == "jet3p":
@@ -402,7 +406,7 @@ def ours(args):
             nb, D = (32, 16, 16), 16.0
             flags, centre = synth.jet_three_level(*nb, r1=(4.0, 16.0), r2=(6.0, 12.0), x1=(0, 96), x2=(0, 48))
         ctx = lbm.lbm_create(model, storage, nb, False, flags, 1.0 / (3 * 8e-5 + 0.5),
-                             0.18 if model == "d3q19" else 0.0, stream.cuda_stream)
+                             0.18 if model == "d3q19" else 0.0, stream.cuda_stream, walls=walls, slip=slip)
         lbm.lbm_set_inflow(ctx, centre[0], centre[1], D, 0.05, 0.01, 389)
         lbm.lbm_step(ctx, W)
         lbm.lbm_set_profiling(ctx, True)
@@ -503,6 +507,9 @@ def ours(args):
             lbm.lbm_destroy(r["ctx"])
         for model in ("d3q27", "d3q19"):
             variants["jet_2level_%s_f32" % model] = run_jet(lbm, torch, model, max(10, K // 4), 3, stream)
+        # the same jet in a tank: no-slip side walls and bottom, free-slip top
+        variants["jet_2level_tank_d3q27_f32"] = run_jet(lbm, torch, "d3q27", max(10, K // 4), 3, stream,
+                                                        walls=15, slip=8)
         for storage in ("f32", "f16"):
             variants["jet_3level_d3q27_%s" % storage] = run_jet3(lbm, torch, storage, max(20, K // 4), 3, stream)
         variants["adjoint_d3q27_f32"] = run_adjoint(lbm, torch, stream)
@@ -574,7 +581,7 @@ def main():
     ap.add_argument("--kernel-only", action="store_true",
                     help="only the stream-collide steps of one variant (for ncu captures)")
     ap.add_argument("--variant", default="d3q27_f32",
-                    help="for --kernel-only: model_storage (e.g. d3q19_f16), jet2s_/jet3s_/jet3p_"
+                    help="for --kernel-only: model_storage (e.g. d3q19_f16), jet2s_/jet2t_/jet3s_/jet3p_"
                          "model_storage, or adjoint")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -58,19 +58,36 @@ typedef enum { LBM_D3Q19_MRT_LES = 0, LBM_D3Q27_FCLB = 1 } lbm_model;
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2 } lbm_storage;
 
 /* Block grid.  Level 0 has nbx*nby*nbz blocks of 8^3 cells; y and z are
- * periodic.  x is periodic when periodic_x != 0; otherwise the face x = 0 is a
- * velocity inflow (lbm_set_inflow; rest velocity until called) and the face
- * x = NX a zero-gradient outflow.  refine concatenates, for l = 0..levels-2,
- * one byte per level-l block (nbx*2^l by nby*2^l by nbz*2^l, x fastest):
- * 1 = the block is split into 8 level-(l+1) blocks.  Rules (checked):
- * flags only on blocks of level l; each level l < levels-1 refines at least
- * one block; for l >= 1 every block touching a refined block belongs to
- * level l (so interpolation stencils stay inside level l). */
+ * periodic unless walls says otherwise.  x is periodic when periodic_x != 0;
+ * otherwise the face x = 0 is a velocity inflow (lbm_set_inflow; rest
+ * velocity until called) and the face x = NX a zero-gradient outflow.
+ * refine concatenates, for l = 0..levels-2, one byte per level-l block
+ * (nbx*2^l by nby*2^l by nbz*2^l, x fastest): 1 = the block is split into 8
+ * level-(l+1) blocks.  Rules (checked): flags only on blocks of level l; each
+ * level l < levels-1 refines at least one block; for l >= 1 every block
+ * touching a refined block belongs to level l (so interpolation stencils stay
+ * inside level l).
+ *
+ * Walls (Section 3.2: the tank's no-slip walls and free-slip top): walls has
+ * bit 0/1 for the low/high y face and bit 2/3 for the low/high z face; the
+ * faces of an axis are walls together or not at all (3, 12 or 15 when set).
+ * slip marks the free-slip walls among them (a subset of walls); the others
+ * are no-slip.  A pull that would cross a wall face is reflected: no-slip by
+ * half-way bounce-back, f_i(x, t+1) = f~_opp(i)(x, t) (the wall lies half a
+ * cell outside the boundary cells); free-slip by specular reflection, the
+ * population with its wall-normal components flipped pulled along the other
+ * axes, f_i(x, t+1) = f~_m(i)(x - e_i + (e_i . n) n, t).  A no-slip crossing
+ * wins over a free-slip one; two free-slip crossings flip both components.
+ * Refined level-0 blocks must keep one block away from the wall faces
+ * (checked).  walls = slip = 0 (a zero-initialised struct) keeps y and z
+ * periodic. */
 typedef struct {
   int nbx, nby, nbz;
   int periodic_x;
   int levels;
   const uint8_t* refine;
+  int walls; /* wall faces, see above; 0 = periodic y and z */
+  int slip;  /* free-slip subset of walls */
 } lbm_grid;
 
 /* Sizes of a grid, computed on the host without touching a GPU. */

@@ -67,7 +67,7 @@ class NestedSolver:
         free-slip walls among them (the others are no-slip)."""
         self.m = Model(model)
         self.Q = self.m.Q
-        if (walls & 3) not in (0, 3) or (walls & 12) not in (0, 12) or (slip & ~walls):
+        if (walls & 3) not in (0, 3) or (walls & 12) not in (0, 12) or (walls & ~15) or (slip & ~walls):
             raise ValueError("walls come in pairs per axis; slip marks a subset of them")
         self.walls, self.slip = int(walls), int(slip)
         refine = list(refine)

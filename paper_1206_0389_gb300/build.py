@@ -13,6 +13,8 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["update.cu", "update_d3q19_f64.cu", "update_d3q19_f32.cu", "update_d3q19_f16.cu",
            "update_d3q27_f64.cu", "update_d3q27_f32.cu", "update_d3q27_f16.cu",
+           "update_walls_d3q19_f64.cu", "update_walls_d3q19_f32.cu", "update_walls_d3q19_f16.cu",
+           "update_walls_d3q27_f64.cu", "update_walls_d3q27_f32.cu", "update_walls_d3q27_f16.cu",
            "interface.cu", "util.cu", "api.cu", "plan.cpp", "noalloc.cu", "adjoint.cu"]
 
 

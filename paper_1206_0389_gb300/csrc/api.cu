@@ -271,6 +271,8 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
     u.force = !c->has_force ? nullptr
               : c->storage == LBM_F64 ? static_cast<const void*>(c->dl[0].force)
                                        : static_cast<const void*>(c->dl[0].force_f);
+    u.walls = c->plan.walls;
+    u.slip = c->plan.slip;
     ops.push_back(up);
     for (int l = lmin; l < L; ++l) par[l] ^= 1;
     // fine-to-coarse after the second substep of each fine level: one launch
@@ -423,7 +425,7 @@ int autotune(lbm_ctx* ctx) {
     bool listed = false;
     for (const auto& sh : shapes) listed |= sh[0] == t && sh[1] == mb;
     int occ = 0;
-    ok = ok && listed && update_occupancy(ctx->model, ctx->storage, t, mb, &occ) == cudaSuccess && occ >= 1;
+    ok = ok && listed && update_occupancy(ctx->model, ctx->storage, ctx->plan.walls != 0, t, mb, &occ) == cudaSuccess && occ >= 1;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (!ok) return fail(ctx, LBM_ERR_ARG, std::string("LBM_LAUNCH_SHAPE not a listed shape: ") + fixed);
@@ -435,7 +437,7 @@ int autotune(lbm_ctx* ctx) {
   for (const auto& sh : shapes) {
     const int t = sh[0], mb = sh[1];
     int occ = 0;
-    if (update_occupancy(ctx->model, ctx->storage, t, mb, &occ) != cudaSuccess || occ < 1) continue;
+    if (update_occupancy(ctx->model, ctx->storage, ctx->plan.walls != 0, t, mb, &occ) != cudaSuccess || occ < 1) continue;
     const int clist[2] = {0, occ * ctx->sms};
     for (int cc : clist) {
       if (launch_update(ctx->model, ctx->storage, big->ua, t, mb, cc, ctx->stream) != cudaSuccess) continue;
@@ -1064,6 +1066,7 @@ int lbm_adjoint_forward(lbm_ctx* ctx, int T, int checkpoint_every) {
   if (!ctx) return LBM_ERR_ARG;
   if (ctx->model != LBM_D3Q27_FCLB || ctx->L != 1 || !ctx->plan.periodic_x)
     return fail(ctx, LBM_ERR_STATE, "the adjoint is defined for single-level periodic D3Q27 grids");
+  if (ctx->plan.walls) return fail(ctx, LBM_ERR_STATE, "the adjoint is defined without walls");
   if (ctx->storage == LBM_F16) return fail(ctx, LBM_ERR_STATE, "the adjoint needs F32 or F64 storage");
   if (T < 1 || checkpoint_every < 1 || checkpoint_every > T)
     return fail(ctx, LBM_ERR_ARG, "need T >= 1 and 1 <= checkpoint_every <= T");

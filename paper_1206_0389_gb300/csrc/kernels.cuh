@@ -51,6 +51,8 @@ struct UpdateArgs {
   double cs2_18;          // 18 Cs^2
   const void* force;      // level 0 body force [3][nblocks*512] (block order) in the
                           // compute type (double for F64 storage, else float) or nullptr
+  int walls, slip;        // level-0 wall faces (bit 0/1 low/high y, 2/3 low/high z) and
+                          // the free-slip ones among them; read by the W = true kernels
 };
 
 // coarse-to-fine work comes in chunks of consecutive ghost cells (sorted by
@@ -175,7 +177,7 @@ struct BCArgs {
 // model: 0 D3Q19 MRT-LES, 1 D3Q27 FCLB; storage: lbm_storage.
 cudaError_t launch_update(int model, int storage, const UpdateArgs& a, int threads, int minb, int ctas,
                           cudaStream_t st);
-cudaError_t update_occupancy(int model, int storage, int threads, int minb, int* ctas_per_sm);
+cudaError_t update_occupancy(int model, int storage, bool walls, int threads, int minb, int* ctas_per_sm);
 cudaError_t launch_c2f(int model, int storage, const C2FArgs& a, cudaStream_t st);
 cudaError_t launch_f2c(int model, int storage, const F2CArgs& a, cudaStream_t st);
 cudaError_t launch_bc(int model, int storage, const BCArgs& a, cudaStream_t st);

@@ -72,6 +72,8 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
   if (g.levels < 1 || g.levels > kMaxL) return "levels must be in 1..4";
   if (g.levels > 1 && g.refine == nullptr) return "refine flags required when levels > 1";
   if (!(omega > 0.0 && omega < 2.0)) return "omega must be in (0, 2)";
+  if ((g.walls & 3) % 3 != 0 || (g.walls & 12) % 12 != 0 || (g.walls & ~15) || (g.slip & ~g.walls))
+    return "walls come in pairs per axis (bits 0|1 for y, 2|3 for z); slip must be a subset of walls";
   const int L = g.levels;
   const int64_t top = int64_t(g.nbx) * g.nby * g.nbz << (3 * (L - 1));
   if (int64_t(g.nbx) << (L - 1) > (1 << 20) || int64_t(g.nby) << (L - 1) > (1 << 20) ||
@@ -84,6 +86,8 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
   P.Q = model == LBM_D3Q19_MRT_LES ? 19 : 27;
   P.levels = L;
   P.periodic_x = g.periodic_x != 0;
+  P.walls = g.walls;
+  P.slip = g.slip;
   const bool px = P.periodic_x;
 
   // ---------------------------------------------------------------- levels
@@ -111,6 +115,16 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
         cnt += v;
       }
       off += n;
+      if (l == 0 && g.walls) {  // refined blocks keep one block away from the walls
+        for (int bz = 0; bz < d.nbz; ++bz)
+          for (int by = 0; by < d.nby; ++by)
+            for (int bx = 0; bx < d.nbx; ++bx)
+              if (d.refined[d.at(bx, by, bz)] && (((g.walls & 3) && (by == 0 || by == d.nby - 1)) ||
+                                                  ((g.walls & 12) && (bz == 0 || bz == d.nbz - 1)))) {
+                snprintf(msg, sizeof msg, "refined block (%d,%d,%d) touches a wall face", bx, by, bz);
+                return msg;
+              }
+      }
       if (cnt == 0) {
         snprintf(msg, sizeof msg, "level %d refines no block", l);
         return msg;

@@ -48,6 +48,7 @@ struct GridPlan {
   int model = 0, storage = 0, Q = 19;
   int levels = 1;
   bool periodic_x = true;
+  int walls = 0, slip = 0;  // level-0 wall faces (bit 0/1 low/high y, 2/3 low/high z), free-slip subset
   std::vector<LevelPlan> lv;
   int64_t device_bytes = 0;
 };

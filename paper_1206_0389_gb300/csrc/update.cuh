@@ -15,6 +15,16 @@
 // + X(e_x) + Y(e_y) + Z(e_z) with X(+1) = Xm, X(-1) = Xp, X(0) = 0.  On the
 // zero-gradient outflow face (Xp = -1 for x == 7) the ghost copy of cell
 // (NX - 1, y', z') is read from that cell directly.
+//
+// Walls (instances with W = true): a pull of a level-0 cell that would cross
+// a y or z wall face of the domain is replaced.  No-slip (half-way
+// bounce-back): f_i(x) = f~_opp(i)(x), the opposite population of the cell
+// itself.  Free-slip (specular reflection): the population with the
+// wall-normal components flipped, pulled along the axes not crossed only,
+// f_i(x) = f~_m(i)(x - e_i + (e_i . n) n).  A no-slip crossing wins over a
+// free-slip one; two free-slip crossings flip both components.  Opposite and
+// mirrored populations have the same weight, so the storage decode of i
+// applies to them unchanged.
 #pragma once
 #include <algorithm>
 #include <type_traits>
@@ -31,7 +41,7 @@ __device__ __forceinline__ __half ldg_half_l2(const __half* p) {
   return __ushort_as_half(v);
 }
 
-template <class M, class S, int TPB, int MINB>
+template <class M, class S, int TPB, int MINB, bool W>
 __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
   using St = Store<S>;
   using T = typename St::T;
@@ -63,6 +73,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
     const int dyp = (w.edges & 8) ? -BX * (L.BY - 1) : BX;
     const int dzm = (w.edges & 16) ? BXY * (L.BZ - 1) : -BXY;
     const int dzp = (w.edges & 32) ? -BXY * (L.BZ - 1) : BXY;
+    // wall faces this block touches (bit 0/1 low/high y, 2/3 low/high z):
+    // the level-0 box is the domain, so its wrapping faces are the walls
+    const int wf = (W && w.level == 0) ? (a.walls & ((w.edges >> 2) & 15)) : 0;
     const T tau0 = T(L.tau0);
     const S* __restrict__ src = reinterpret_cast<const S*>(L.src) + int64_t(w.block) * QS;
     S* __restrict__ dst = reinterpret_cast<S*>(L.dst) + int64_t(w.block) * QS;
@@ -81,17 +94,39 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
       int Xm, Xp, Ym, Yp, Zm, Zp;
       offsets(c, Xm, Xp, Ym, Yp, Zm, Zp);
       const S* p = src + c;
+      // the cell's wall crossings: pulls with e_y = +1 cross the low y face
+      // from y == 0, e_y = -1 the high one from y == 7, likewise z
+      bool yl = false, yh = false, zl = false, zh = false;
+      if constexpr (W) {
+        const int y = (c >> 3) & 7, z = c >> 6;
+        yl = (wf & 1) && y == 0;
+        yh = (wf & 2) && y == 7;
+        zl = (wf & 4) && z == 0;
+        zh = (wf & 8) && z == 7;
+      }
       static_for<Q>([&](auto i) {
         constexpr int ex = Lattice<Q>::ex(i), ey = Lattice<Q>::ey(i), ez = Lattice<Q>::ez(i);
         constexpr int k = int(i) * kCells - (ex + 8 * ey + 64 * ez);
-        int o = 0;
-        if constexpr (ex == 1) o += Xm;
-        if constexpr (ex == -1) o += Xp;
-        if constexpr (ey == 1) o += Ym;
-        if constexpr (ey == -1) o += Yp;
-        if constexpr (ez == 1) o += Zm;
-        if constexpr (ez == -1) o += Zp;
-        load(i, p + o + k);
+        const int X = ex == 1 ? Xm : ex == -1 ? Xp : 0;
+        const int Y = ey == 1 ? Ym : ey == -1 ? Yp : 0;
+        const int Z = ez == 1 ? Zm : ez == -1 ? Zp : 0;
+        int o = X + Y + Z + k;
+        if constexpr (W && (ey != 0 || ez != 0)) {
+          const bool cy = ey == 1 ? yl : ey == -1 ? yh : false;
+          const bool cz = ez == 1 ? zl : ez == -1 ? zh : false;
+          if (cy || cz) {
+            const bool sy = a.slip & (ey == 1 ? 1 : 2), sz = a.slip & (ez == 1 ? 4 : 8);
+            constexpr int ib = Lattice<Q>::index(-ex, -ey, -ez);
+            constexpr int iy = Lattice<Q>::index(ex, -ey, ez);
+            constexpr int iz = Lattice<Q>::index(ex, ey, -ez);
+            constexpr int iyz = Lattice<Q>::index(ex, -ey, -ez);
+            if ((cy && !sy) || (cz && !sz)) o = ib * kCells;
+            else if (cy && cz) o = iyz * kCells - ex + X;
+            else if (cy) o = iy * kCells - (ex + 64 * ez) + X + Z;
+            else o = iz * kCells - (ex + 8 * ey) + X + Y;
+          }
+        }
+        load(i, p + o);
       });
     };
     auto active = [&](int c) {
@@ -163,39 +198,52 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
 // Launch shapes the autotuner chooses from: threads per CTA, and a minimum
 // number of resident CTAs per SM that caps the registers (higher occupancy
 // for the FP16 variants, whose half-size loads keep fewer bytes in flight).
-template <class M, class S>
+template <class M, class S, bool W>
 cudaError_t launch_ms(const UpdateArgs& a, int threads, int minb, int ctas, cudaStream_t st) {
   if (a.nitems == 0) return cudaSuccess;
   const int grid = ctas > 0 ? std::min(ctas, a.nitems) : a.nitems;
-  if (threads == 128 && minb == 7) k_update<M, S, 128, 7><<<grid, 128, 0, st>>>(a);
-  else if (threads == 128 && minb == 1) k_update<M, S, 128, 1><<<grid, 128, 0, st>>>(a);
-  else if (threads == 256 && minb == 1) k_update<M, S, 256, 1><<<grid, 256, 0, st>>>(a);
-  else if (threads == 128 && minb == 8) k_update<M, S, 128, 8><<<grid, 128, 0, st>>>(a);
-  else if (threads == 256 && minb == 4) k_update<M, S, 256, 4><<<grid, 256, 0, st>>>(a);
+  if (threads == 128 && minb == 7) k_update<M, S, 128, 7, W><<<grid, 128, 0, st>>>(a);
+  else if (threads == 128 && minb == 1) k_update<M, S, 128, 1, W><<<grid, 128, 0, st>>>(a);
+  else if (threads == 256 && minb == 1) k_update<M, S, 256, 1, W><<<grid, 256, 0, st>>>(a);
+  else if (threads == 128 && minb == 8) k_update<M, S, 128, 8, W><<<grid, 128, 0, st>>>(a);
+  else if (threads == 256 && minb == 4) k_update<M, S, 256, 4, W><<<grid, 256, 0, st>>>(a);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
-template <class M, class S>
+template <class M, class S, bool W>
 cudaError_t occ_ms(int threads, int minb, int* n) {
-  if (threads == 128 && minb == 7) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 7>, 128, 0);
-  if (threads == 128 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 1>, 128, 0);
-  if (threads == 256 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 256, 1>, 256, 0);
-  if (threads == 128 && minb == 8) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 8>, 128, 0);
-  if (threads == 256 && minb == 4) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 256, 4>, 256, 0);
+  if (threads == 128 && minb == 7) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 7, W>, 128, 0);
+  if (threads == 128 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 1, W>, 128, 0);
+  if (threads == 256 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 256, 1, W>, 256, 0);
+  if (threads == 128 && minb == 8) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 8, W>, 128, 0);
+  if (threads == 256 && minb == 4) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 256, 4, W>, 256, 0);
   return cudaErrorInvalidValue;
 }
 
-// one translation unit per (model, storage) instantiates these
+// one translation unit per (model, storage) instantiates the periodic
+// kernels, another the wall kernels (update_walls_<model>_<storage>.cu)
 #define LBM_UPDATE_INSTANCE(M, S, NAME)                                                               \
   cudaError_t launch_update_##NAME(const UpdateArgs& a, int threads, int minb, int ctas, cudaStream_t st) { \
-    return launch_ms<M, S>(a, threads, minb, ctas, st);                                              \
+    return launch_ms<M, S, false>(a, threads, minb, ctas, st);                                       \
   }                                                                                                  \
-  cudaError_t occupancy_update_##NAME(int threads, int minb, int* n) { return occ_ms<M, S>(threads, minb, n); }
+  cudaError_t occupancy_update_##NAME(int threads, int minb, int* n) { return occ_ms<M, S, false>(threads, minb, n); }
+
+#define LBM_UPDATE_WALL_INSTANCE(M, S, NAME)                                                          \
+  cudaError_t launch_update_walls_##NAME(const UpdateArgs& a, int threads, int minb, int ctas,        \
+                                         cudaStream_t st) {                                          \
+    return launch_ms<M, S, true>(a, threads, minb, ctas, st);                                        \
+  }                                                                                                  \
+  cudaError_t occupancy_update_walls_##NAME(int threads, int minb, int* n) {                         \
+    return occ_ms<M, S, true>(threads, minb, n);                                                     \
+  }
 
 #define LBM_UPDATE_DECL(NAME)                                                                          \
   cudaError_t launch_update_##NAME(const UpdateArgs& a, int threads, int minb, int ctas, cudaStream_t st); \
-  cudaError_t occupancy_update_##NAME(int threads, int minb, int* n);
+  cudaError_t occupancy_update_##NAME(int threads, int minb, int* n);                                   \
+  cudaError_t launch_update_walls_##NAME(const UpdateArgs& a, int threads, int minb, int ctas,          \
+                                         cudaStream_t st);                                             \
+  cudaError_t occupancy_update_walls_##NAME(int threads, int minb, int* n);
 
 LBM_UPDATE_DECL(d3q19_f64)
 LBM_UPDATE_DECL(d3q19_f32)

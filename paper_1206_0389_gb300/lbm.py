@@ -37,7 +37,7 @@ class LbmError(RuntimeError):
 
 class lbm_grid(ctypes.Structure):
     _fields_ = [("nbx", c_int), ("nby", c_int), ("nbz", c_int), ("periodic_x", c_int),
-                ("levels", c_int), ("refine", POINTER(c_uint8))]
+                ("levels", c_int), ("refine", POINTER(c_uint8)), ("walls", c_int), ("slip", c_int)]
 
 
 class lbm_plan_info(ctypes.Structure):
@@ -109,19 +109,21 @@ def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
 
 
-def make_grid(nb, periodic_x=True, refine=()):
-    """lbm_grid from coarse block counts nb = (nbx, nby, nbz) and refine flags
-    (list of arrays shaped (nbz*2^l, nby*2^l, nbx*2^l)).  Returns (grid, keepalive)."""
+def make_grid(nb, periodic_x=True, refine=(), walls=0, slip=0):
+    """lbm_grid from coarse block counts nb = (nbx, nby, nbz), refine flags
+    (list of arrays shaped (nbz*2^l, nby*2^l, nbx*2^l)) and the wall faces
+    (bit 0/1 low/high y, 2/3 low/high z; slip the free-slip subset).
+    Returns (grid, keepalive)."""
     flags = [np.ascontiguousarray(np.asarray(r, dtype=np.uint8)).reshape(-1) for r in refine]
     buf = np.concatenate(flags) if flags else np.zeros(1, dtype=np.uint8)
     g = lbm_grid(int(nb[0]), int(nb[1]), int(nb[2]), 1 if periodic_x else 0, len(flags) + 1,
-                 buf.ctypes.data_as(POINTER(c_uint8)))
+                 buf.ctypes.data_as(POINTER(c_uint8)), int(walls), int(slip))
     return g, buf
 
 
-def lbm_plan(nb, periodic_x=True, refine=(), model="d3q19", storage="f32"):
+def lbm_plan(nb, periodic_x=True, refine=(), model="d3q19", storage="f32", walls=0, slip=0):
     lib = load()
-    g, keep = make_grid(nb, periodic_x, refine)
+    g, keep = make_grid(nb, periodic_x, refine, walls, slip)
     info = lbm_plan_info()
     st = lib.lbm_plan(ctypes.byref(g), MODELS[model], STORAGES[storage], ctypes.byref(info))
     if st != LBM_OK:
@@ -154,9 +156,10 @@ def _check(ctx, st):
         raise LbmError(st, msg.decode() if msg else "")
 
 
-def lbm_create(model, storage, nb, periodic_x=True, refine=(), omega=1.0, cs=0.0, stream=None):
+def lbm_create(model, storage, nb, periodic_x=True, refine=(), omega=1.0, cs=0.0, stream=None,
+               walls=0, slip=0):
     lib = load()
-    g, keep = make_grid(nb, periodic_x, refine)
+    g, keep = make_grid(nb, periodic_x, refine, walls, slip)
     h = c_void_p()
     st = lib.lbm_create(ctypes.byref(h), MODELS[model], STORAGES[storage], ctypes.byref(g),
                         float(omega), float(cs), stream)

@@ -14,12 +14,13 @@ def gpu():
     return lbm
 
 
-def make_pair(model, storage, nb, periodic_x=True, refine=(), omega=1.6, cs=0.0):
+def make_pair(model, storage, nb, periodic_x=True, refine=(), omega=1.6, cs=0.0, walls=0, slip=0):
     lbm = gpu()
-    ctx = lbm.lbm_create(model, storage, nb, periodic_x, [np.asarray(r) for r in refine], omega, cs)
+    ctx = lbm.lbm_create(model, storage, nb, periodic_x, [np.asarray(r) for r in refine], omega, cs,
+                         walls=walls, slip=slip)
     orc = NestedSolver(model, nb, periodic_x=periodic_x,
                        refine=[torch.as_tensor(np.asarray(r)).bool() for r in refine],
-                       omega=omega, cs=cs)
+                       omega=omega, cs=cs, walls=walls, slip=slip)
     return ctx, orc
 
 

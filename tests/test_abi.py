@@ -10,6 +10,7 @@ import torch
 
 import synth
 from oracle.grid import build_levels
+from oracle.solver import NestedSolver
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 lbm = pytest.importorskip("paper_1206_0389_gb300.lbm")
@@ -96,6 +97,44 @@ def test_plan_rejects_bad_grids():
         lbm.lbm_plan((3, 2, 2), True, [bad, np.zeros((4, 4, 6), dtype=bool)])
     with pytest.raises(lbm.LbmError):
         lbm.lbm_plan((0, 2, 2), True, [])
+
+
+@pytest.mark.parametrize("walls,slip,ok", [(0, 0, True), (3, 0, True), (12, 12, True), (15, 9, True),
+                                            (1, 0, False), (6, 0, False), (3, 4, False), (16, 0, False)])
+def test_plan_wall_rules_match_oracle(walls, slip, ok):
+    """Walls come in pairs per axis and slip is a subset of them: the planner
+    and the oracle accept and reject the same settings."""
+    try:
+        NestedSolver("d3q27", (2, 2, 2), walls=walls, slip=slip)
+        oracle_ok = True
+    except ValueError:
+        oracle_ok = False
+    assert oracle_ok == ok
+    if ok:
+        lbm.lbm_plan((2, 2, 2), True, [], walls=walls, slip=slip)
+    else:
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_plan((2, 2, 2), True, [], walls=walls, slip=slip)
+
+
+def test_plan_rejects_refinement_next_to_walls():
+    r = np.zeros((3, 3, 4), dtype=bool)
+    r[1, 1, 0:2] = True                      # one block away from every y/z face
+    lbm.lbm_plan((4, 3, 3), False, [r], walls=15, slip=8)
+    NestedSolver("d3q27", (4, 3, 3), periodic_x=False, refine=[torch.from_numpy(r)], walls=15)
+    for bad_wall in (3, 12):
+        r2 = r.copy()
+        if bad_wall == 3:
+            r2[1, 0, 0] = True                   # touches the low y face
+        else:
+            r2[2, 1, 0] = True                   # touches the high z face
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_plan((4, 3, 3), False, [r2], walls=bad_wall)
+        with pytest.raises(ValueError):
+            NestedSolver("d3q27", (4, 3, 3), periodic_x=False, refine=[torch.from_numpy(r2)],
+                         walls=bad_wall)
+        # the same refinement is fine while that axis stays periodic
+        lbm.lbm_plan((4, 3, 3), False, [r2], walls=15 - bad_wall)
 
 
 def test_create_without_gpu_reports_cuda_error():
