@@ -17,7 +17,8 @@
 // (NX - 1, y', z') is read from that cell directly.
 //
 // Walls (instances with W = true): a pull of a level-0 cell that would cross
-// a y or z wall face of the domain is replaced.  No-slip (half-way
+// a y or z wall face of the domain is replaced after the periodic pull, for
+// the cells next to a wall only.  No-slip (half-way
 // bounce-back): f_i(x) = f~_opp(i)(x), the opposite population of the cell
 // itself.  Free-slip (specular reflection): the population with the
 // wall-normal components flipped, pulled along the axes not crossed only,
@@ -94,45 +95,58 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
       int Xm, Xp, Ym, Yp, Zm, Zp;
       offsets(c, Xm, Xp, Ym, Yp, Zm, Zp);
       const S* p = src + c;
-      // the cell's wall crossings: pulls with e_y = +1 cross the low y face
-      // from y == 0, e_y = -1 the high one from y == 7, likewise z
-      bool yl = false, yh = false, zl = false, zh = false;
-      if constexpr (W) {
-        const int y = (c >> 3) & 7, z = c >> 6;
-        yl = (wf & 1) && y == 0;
-        yh = (wf & 2) && y == 7;
-        zl = (wf & 4) && z == 0;
-        zh = (wf & 8) && z == 7;
-      }
       static_for<Q>([&](auto i) {
         constexpr int ex = Lattice<Q>::ex(i), ey = Lattice<Q>::ey(i), ez = Lattice<Q>::ez(i);
         constexpr int k = int(i) * kCells - (ex + 8 * ey + 64 * ez);
-        const int X = ex == 1 ? Xm : ex == -1 ? Xp : 0;
-        const int Y = ey == 1 ? Ym : ey == -1 ? Yp : 0;
-        const int Z = ez == 1 ? Zm : ez == -1 ? Zp : 0;
-        int o = X + Y + Z + k;
-        if constexpr (W && (ey != 0 || ez != 0)) {
-          const bool cy = ey == 1 ? yl : ey == -1 ? yh : false;
-          const bool cz = ez == 1 ? zl : ez == -1 ? zh : false;
-          if (cy || cz) {
-            const bool sy = a.slip & (ey == 1 ? 1 : 2), sz = a.slip & (ez == 1 ? 4 : 8);
-            constexpr int ib = Lattice<Q>::index(-ex, -ey, -ez);
-            constexpr int iy = Lattice<Q>::index(ex, -ey, ez);
-            constexpr int iz = Lattice<Q>::index(ex, ey, -ez);
-            constexpr int iyz = Lattice<Q>::index(ex, -ey, -ez);
-            if ((cy && !sy) || (cz && !sz)) o = ib * kCells;
-            else if (cy && cz) o = iyz * kCells - ex + X;
-            else if (cy) o = iy * kCells - (ex + 64 * ez) + X + Z;
-            else o = iz * kCells - (ex + 8 * ey) + X + Y;
-          }
-        }
-        load(i, p + o);
+        int o = 0;
+        if constexpr (ex == 1) o += Xm;
+        if constexpr (ex == -1) o += Xp;
+        if constexpr (ey == 1) o += Ym;
+        if constexpr (ey == -1) o += Yp;
+        if constexpr (ez == 1) o += Zm;
+        if constexpr (ez == -1) o += Zp;
+        load(i, p + o + k);
       });
     };
     auto active = [&](int c) {
       if (w.mask < 0) return true;
       const uint32_t m = __ldg(a.masks + w.mask * 16 + (c >> 5));
       return bool((m >> (c & 31)) & 1u);
+    };
+    // replaces, for a cell next to a wall face, the populations whose pull
+    // crossed it (the periodic pull above read a valid but unused value)
+    auto wall_fix = [&](int c, T (&g)[Q]) {
+      const int y = (c >> 3) & 7, z = c >> 6;
+      const bool yl = (wf & 1) && y == 0, yh = (wf & 2) && y == 7;
+      const bool zl = (wf & 4) && z == 0, zh = (wf & 8) && z == 7;
+      if (!(yl || yh || zl || zh)) return;
+      int Xm, Xp, Ym, Yp, Zm, Zp;
+      offsets(c, Xm, Xp, Ym, Yp, Zm, Zp);
+      const S* p = src + c;
+      static_for<Q>([&](auto i) {
+        constexpr int ex = Lattice<Q>::ex(i), ey = Lattice<Q>::ey(i), ez = Lattice<Q>::ez(i);
+        if constexpr (ey != 0 || ez != 0) {
+          const bool cy = ey == 1 ? yl : ey == -1 ? yh : false;
+          const bool cz = ez == 1 ? zl : ez == -1 ? zh : false;
+          if (cy || cz) {
+            const bool sy = a.slip & (ey == 1 ? 1 : 2), sz = a.slip & (ez == 1 ? 4 : 8);
+            const int X = ex == 1 ? Xm : ex == -1 ? Xp : 0;
+            const int Y = ey == 1 ? Ym : ey == -1 ? Yp : 0;
+            const int Z = ez == 1 ? Zm : ez == -1 ? Zp : 0;
+            constexpr int ib = Lattice<Q>::index(-ex, -ey, -ez);
+            constexpr int iy = Lattice<Q>::index(ex, -ey, ez);
+            constexpr int iz = Lattice<Q>::index(ex, ey, -ez);
+            constexpr int iyz = Lattice<Q>::index(ex, -ey, -ez);
+            int o;
+            if ((cy && !sy) || (cz && !sz)) o = ib * kCells;
+            else if (cy && cz) o = iyz * kCells - ex + X;
+            else if (cy) o = iy * kCells - (ex + 64 * ez) + X + Z;
+            else o = iz * kCells - (ex + 8 * ey) + X + Y;
+            if constexpr (kScaled) g[i] = __half2float(__ldg(p + o));
+            else g[i] = St::template get<Q, i>(p + o);
+          }
+        }
+      });
     };
     auto collide_store = [&](int c, T (&g)[Q]) {
       if constexpr (Q == 19) {
@@ -165,6 +179,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
         if (active(c)) {
           T g[Q];
           static_for<Q>([&](auto i) { g[i] = __half2float(cur[i]); });
+          if constexpr (W) if (wf) wall_fix(c, g);
           collide_store(c, g);
         }
         static_for<Q>([&](auto i) { cur[i] = nxt[i]; });
@@ -189,6 +204,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
           if constexpr (kScaled) g[i] = __half2float(ldg_half_l2(p));
           else g[i] = St::template get<Q, i>(p);
         });
+        if constexpr (W) if (wf) wall_fix(c, g);
         collide_store(c, g);
       }
     }

@@ -96,8 +96,11 @@ def test_single_step_f16(model, variant, monkeypatch):
 
 
 @pytest.mark.parametrize("model", MODELS)
-def test_graph_and_direct_launches_agree(model):
-    """The CUDA-graph path and the profiled direct-launch path are identical."""
+def test_graph_and_direct_launches_agree(model, monkeypatch):
+    """The CUDA-graph path and the profiled direct-launch path are identical
+    (for one launch shape: the autotuner of each context may pick another,
+    and register-capped shapes may round differently)."""
+    monkeypatch.setenv("LBM_LAUNCH_SHAPE", "128,1,0")
     lbm = gpu()
     nb = (2, 2, 2)
     st = random_state(model, dims(nb), 3, 0.2)
@@ -116,11 +119,12 @@ def test_graph_and_direct_launches_agree(model):
 
 
 @pytest.mark.parametrize("model", MODELS)
-def test_nested_graph_and_direct_launches_agree(model):
+def test_nested_graph_and_direct_launches_agree(model, monkeypatch):
     """A nested grid with inflow whose refined patch meets the inflow face:
     the coarse-step graph (inflow launch beside the coarse-to-fine launch,
     inflow ghosts fed by ghost cells written by the latter) gives the same
-    bits as the sequential launches of the profiled path."""
+    bits as the sequential launches of the profiled path (one launch shape)."""
+    monkeypatch.setenv("LBM_LAUNCH_SHAPE", "128,1,0")
     lbm = gpu()
     nb = (4, 3, 3)
     r = np.zeros((3, 3, 4), dtype=bool)
