@@ -48,6 +48,14 @@ free-slip face by specular reflection, the population with the wall-normal
 velocity component flipped, pulled from the same layer, f_i(x, t+1) =
 f~_m(i)(x - e_i + (e_i . n) n, t).  Where a link crosses two walls, a no-slip
 crossing wins; two free-slip crossings reflect both components.
+
+Pressure outlet (Section 3.2 replaces the tank's weir by a fixed pressure; the
+scheme is not given): with outlet = 1 the ghost column x = NX of level 0
+holds the equilibrium at the fixed density rho_out with the velocity of the
+cell x = NX - 1, plus that cell's non-equilibrium part,
+f_ghost = f_eq(rho_out, u_N) + (f_N - f_eq(rho_N, u_N)) (extrapolation of the
+non-equilibrium part).  Its density is rho_out and its velocity u_N.  Refined
+level-0 blocks keep one block away from the outlet face.
 """
 import math
 
@@ -61,16 +69,24 @@ from .rng import inflow_xi
 
 
 class NestedSolver:
-    def __init__(self, model, nb, periodic_x=True, refine=(), omega=1.0, cs=0.0, walls=0, slip=0):
+    def __init__(self, model, nb, periodic_x=True, refine=(), omega=1.0, cs=0.0, walls=0, slip=0,
+                 outlet=0):
         """walls: bit 0/1 the low/high y face, bit 2/3 the low/high z face are
         walls (both faces of an axis or neither); slip: the same bits mark the
-        free-slip walls among them (the others are no-slip)."""
+        free-slip walls among them (the others are no-slip).  outlet: 0
+        zero-gradient outflow, 1 fixed-pressure outlet (non-periodic x)."""
         self.m = Model(model)
         self.Q = self.m.Q
         if (walls & 3) not in (0, 3) or (walls & 12) not in (0, 12) or (walls & ~15) or (slip & ~walls):
             raise ValueError("walls come in pairs per axis; slip marks a subset of them")
         self.walls, self.slip = int(walls), int(slip)
+        if outlet not in (0, 1) or (outlet and periodic_x):
+            raise ValueError("outlet is 0 (zero-gradient) or 1 (fixed pressure, non-periodic x)")
+        self.outlet = int(outlet)
+        self.rho_out = 1.0
         refine = list(refine)
+        if outlet and refine and bool(refine[0].bool()[:, :, -1].any()):
+            raise ValueError("refined blocks must keep one block away from the pressure outlet")
         if walls and refine:
             r0 = refine[0].bool()
             near = torch.zeros_like(r0)
@@ -111,6 +127,12 @@ class NestedSolver:
             raise ValueError("inflow needs a non-periodic x axis")
         self.inflow = dict(y0=float(y0), z0=float(z0), D=float(D), u_in=float(u_in),
                            perturb=float(perturb), seed=int(seed))
+
+    def set_outlet(self, rho_out):
+        """Density held at the pressure outlet (full density for both models)."""
+        if not self.outlet:
+            raise ValueError("the grid has no pressure outlet")
+        self.rho_out = float(rho_out)
 
     def set_force(self, F):
         """Per-cell body force (3, NZ, NY, NX) on a single-level FCLB grid."""
@@ -167,10 +189,22 @@ class NestedSolver:
                              p["u_in"] * p["perturb"] * xi[2]])
             u = torch.where(inside[None], u, torch.zeros_like(u))
             f[:, zz, yy, 0] = self.m.feq(rl, u)
-        # outflow column x = NX (index NX+1) copies cell x = NX-1 (index NX)
+        # outflow column x = NX (index NX+1) from cell x = NX-1 (index NX):
+        # a copy (zero gradient), or at the pressure outlet the equilibrium at
+        # rho_out with the cell's velocity plus the cell's non-equilibrium part
         zz, yy = torch.nonzero(src_ok[:, :, lv.NX], as_tuple=True)
         if len(zz):
-            f[:, zz, yy, lv.NX + 1] = f[:, zz, yy, lv.NX]
+            src = f[:, zz, yy, lv.NX]
+            f[:, zz, yy, lv.NX + 1] = self._outlet_ghost(src) if self.outlet else src
+
+    def _outlet_ghost(self, src):
+        """Pressure-outlet ghosts from the cells x = NX - 1 (Q, n): the
+        equilibrium at rho_out with the cell's velocity plus the cell's
+        non-equilibrium part."""
+        u = self.m.velocity(src)
+        rl_n = self.m.density_like(src)
+        rl_out = torch.full_like(rl_n, self.rho_out - 1.0 if self.m.name == "d3q19" else self.rho_out)
+        return self.m.feq(rl_out, u) + (src - self.m.feq(rl_n, u))
 
     def _vel_index(self, ex, ey, ez):
         for q in range(self.Q):

@@ -162,3 +162,40 @@ def test_free_slip_flipping_the_tangential_component_is_caught(monkeypatch):
     orig_wall = S.NestedSolver._wall_pulls
     monkeypatch.setattr(S.NestedSolver, "_wall_pulls", wall_pulls)
     assert fails(TW.test_free_slip_keeps_tangential_uniform_flow, "d3q27")
+
+
+def _plant_outlet(monkeypatch, ghost):
+    monkeypatch.setattr(S.NestedSolver, "_outlet_ghost", ghost)
+
+
+def test_outlet_without_non_equilibrium_part_is_caught(monkeypatch):
+    """A pressure outlet that keeps only the equilibrium at rho_out."""
+    from tests import test_oracle_outlet as TO
+
+    def ghost(self, src):
+        rl = torch.full_like(src[0], self.rho_out - 1.0 if self.m.name == "d3q19" else self.rho_out)
+        return self.m.feq(rl, self.m.velocity(src))
+    _plant_outlet(monkeypatch, ghost)
+    assert fails(TO.test_outlet_cell_of_x_invariant_state_evolves_as_periodic, "d3q27")
+    assert fails(TO.test_outlet_ghost_has_outlet_density_and_cell_velocity, "d3q19")
+
+
+def test_outlet_that_copies_the_cell_is_caught(monkeypatch):
+    """A 'pressure' outlet that is the zero-gradient copy (rho_out unused)."""
+    from tests import test_oracle_outlet as TO
+    _plant_outlet(monkeypatch, lambda self, src: src.clone())
+    assert fails(TO.test_outlet_drains_overpressure_to_rho_out, "d3q27")
+    assert fails(TO.test_outlet_ghost_has_outlet_density_and_cell_velocity, "d3q27")
+
+
+def test_outlet_with_the_density_correction_reversed_is_caught(monkeypatch):
+    from tests import test_oracle_outlet as TO
+
+    def ghost(self, src):
+        u = self.m.velocity(src)
+        rl_n = self.m.density_like(src)
+        rl = torch.full_like(rl_n, self.rho_out - 1.0 if self.m.name == "d3q19" else self.rho_out)
+        return src - (self.m.feq(rl, u) - self.m.feq(rl_n, u))
+    _plant_outlet(monkeypatch, ghost)
+    assert fails(TO.test_outlet_ghost_has_outlet_density_and_cell_velocity, "d3q19")
+    assert fails(TO.test_outlet_drains_overpressure_to_rho_out, "d3q27")
