@@ -80,7 +80,15 @@ typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2 } lbm_storage;
  * wins over a free-slip one; two free-slip crossings flip both components.
  * Refined level-0 blocks must keep one block away from the wall faces
  * (checked).  walls = slip = 0 (a zero-initialised struct) keeps y and z
- * periodic. */
+ * periodic.
+ *
+ * Outlet (Section 3.2 holds the tank's outflow at a fixed pressure): outlet
+ * = 0 keeps the zero-gradient outflow; outlet = 1 (non-periodic x only)
+ * makes the face x = NX a pressure outlet whose ghost cells hold the
+ * equilibrium at the outlet density (lbm_set_outlet; 1 until called) with
+ * the velocity of the cell x = NX - 1 plus that cell's non-equilibrium part,
+ * f_ghost = f_eq(rho_out, u_N) + f_N - f_eq(rho_N, u_N).  Refined level-0
+ * blocks must keep one block away from that face (checked). */
 typedef struct {
   int nbx, nby, nbz;
   int periodic_x;
@@ -88,6 +96,7 @@ typedef struct {
   const uint8_t* refine;
   int walls; /* wall faces, see above; 0 = periodic y and z */
   int slip;  /* free-slip subset of walls */
+  int outlet; /* 0 zero-gradient outflow, 1 fixed-pressure outlet */
 } lbm_grid;
 
 /* Sizes of a grid, computed on the host without touching a GPU. */
@@ -99,7 +108,8 @@ typedef struct {
   int64_t updated_cells[LBM_MAX_LEVELS]; /* active + hidden layer 1                 */
   int64_t hidden_cells[LBM_MAX_LEVELS];  /* hidden layers 1 and 2                   */
   int64_t ghost_cells[LBM_MAX_LEVELS];   /* coarse-to-fine ghost cells              */
-  int64_t bc_cells[LBM_MAX_LEVELS];      /* inflow ghost cells (x = -1)             */
+  int64_t bc_cells[LBM_MAX_LEVELS];      /* inflow (x = -1) and pressure-outlet     */
+                                         /* (x = NX) ghost cells                    */
   int64_t updates_per_coarse_step;       /* sum_l updated_cells[l] * 2^l            */
   int64_t active_updates_per_coarse_step;/* sum_l active_cells[l] * 2^l             */
   int64_t device_bytes;                  /* device memory lbm_create would allocate */
@@ -129,6 +139,12 @@ const char* lbm_create_error(void);
  * substep, y + NY_l z, component).  LBM_ERR_STATE if x is periodic. */
 int lbm_set_inflow(lbm_ctx* ctx, double y0, double z0, double diameter, double u_in,
                    double perturb, uint64_t seed);
+
+/* Density held at the pressure outlet (full density for both models; the
+ * D3Q19 model holds delta rho = rho_out - 1).  LBM_ERR_STATE if the grid has
+ * no pressure outlet (lbm_grid.outlet = 0); LBM_ERR_ARG unless 0.5 < rho_out
+ * < 2; LBM_ERR_NONFINITE on NaN/Inf.  Takes effect at the next lbm_step. */
+int lbm_set_outlet(lbm_ctx* ctx, double rho_out);
 
 /* f = f_eq(rho, u) on every in-domain cell of a level (host arrays: rho
  * [NZ][NY][NX], u [3][NZ][NY][NX]; NULL = rest).  rho is the full density for

@@ -82,6 +82,7 @@ struct lbm_ctx {
   long long stats_n = 0;  // samples in the statistics sums
   // inflow
   double y0 = 0, z0 = 0, diameter = 0, u_in = 0, perturb = 0;
+  double rho_out = 1.0;  // pressure outlet density
   uint64_t seed = 0;
   // launch configuration
   int threads = 256, minb = 1, ctas = 0;
@@ -236,6 +237,7 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
       b.u_in = c->u_in;
       b.perturb = c->perturb;
       b.seed = c->seed;
+      b.rl_out = c->rho_out - 1.0;
       for (int l = lmin; l < L; ++l) {
         const LevelPlan& lp = c->plan.lv[l];
         if (lp.bc.empty()) continue;
@@ -722,6 +724,16 @@ int lbm_set_inflow(lbm_ctx* ctx, double y0, double z0, double diameter, double u
   ctx->u_in = u_in;
   ctx->perturb = perturb;
   ctx->seed = seed;
+  ctx->graphs_valid = false;
+  return LBM_OK;
+}
+
+int lbm_set_outlet(lbm_ctx* ctx, double rho_out) {
+  if (!ctx) return LBM_ERR_ARG;
+  if (!ctx->plan.outlet) return fail(ctx, LBM_ERR_STATE, "the grid has no pressure outlet");
+  if (!std::isfinite(rho_out)) return fail(ctx, LBM_ERR_NONFINITE, "non-finite outlet density");
+  if (!(rho_out > 0.5 && rho_out < 2.0)) return fail(ctx, LBM_ERR_ARG, "outlet density out of range");
+  ctx->rho_out = rho_out;
   ctx->graphs_valid = false;
   return LBM_OK;
 }

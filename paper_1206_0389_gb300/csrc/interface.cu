@@ -346,34 +346,61 @@ __global__ void __launch_bounds__(128) k_bc(const BCArgs a) {
   const S* src = f + int64_t(it.sblock) * QS + it.scell;
   S* dst = f + int64_t(it.gblock) * QS + it.gcell;
   constexpr int NJ = (Q + kBCLanes - 1) / kBCLanes;
-  T part = T(0);
+  // density-like sum and momentum of the source cell (the momentum serves
+  // the pressure outlet only)
+  T part = T(0), jx = T(0), jy = T(0), jz = T(0);
+  T gs[NJ];
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     const int q = r + kBCLanes * j;
-    if (q < Q) part += lane_load(src + q * kCells, Lane<T, Q>(q));
+    const Lane<T, Q> ln(q);
+    gs[j] = q < Q ? lane_load(src + q * kCells, ln) : T(0);
+    part += gs[j];
+    jx += T(ln.x) * gs[j];
+    jy += T(ln.y) * gs[j];
+    jz += T(ln.z) * gs[j];
   }
-  part += __shfl_xor_sync(0xffffffffu, part, 1);
-  part += __shfl_xor_sync(0xffffffffu, part, 2);
-  part += __shfl_xor_sync(0xffffffffu, part, 4);
+#pragma unroll
+  for (int m = 1; m < kBCLanes; m <<= 1) {
+    part += __shfl_xor_sync(0xffffffffu, part, m);
+    jx += __shfl_xor_sync(0xffffffffu, jx, m);
+    jy += __shfl_xor_sync(0xffffffffu, jy, m);
+    jz += __shfl_xor_sync(0xffffffffu, jz, m);
+  }
   const T rl = part;
-  // the disc test and the draws run in double on lanes 0..2 of the group
-  // only (lane c computes velocity component c): FP64 throughput is scarce
-  // on this part
+  // inflow: the disc test and the draws run in double on lanes 0..2 of the
+  // group only (lane c computes velocity component c): FP64 throughput is
+  // scarce on this part.  Every lane takes part in the shuffles (groups of
+  // both item types may share a warp).
   T uc = T(0);
-  if (r < 3)
+  if (it.type == 0 && r < 3)
     uc = T(inflow_u(a.step, a.y0, a.z0, a.r2, a.u_in, a.perturb, a.seed, L.level, L.substep, L.NY, L.inv_scale,
                     it.y, it.z, r));
   const int g0 = int(threadIdx.x & 31) & ~(kBCLanes - 1);
-  const T ux = __shfl_sync(0xffffffffu, uc, g0);
-  const T uy = __shfl_sync(0xffffffffu, uc, g0 + 1);
-  const T uz = __shfl_sync(0xffffffffu, uc, g0 + 2);
+  T ux = __shfl_sync(0xffffffffu, uc, g0);
+  T uy = __shfl_sync(0xffffffffu, uc, g0 + 1);
+  T uz = __shfl_sync(0xffffffffu, uc, g0 + 2);
+  const bool outlet = it.type == 1;
+  if (outlet) {
+    // pressure outlet: the source cell's velocity, u_N = j / rho for the
+    // compressible D3Q27 model, j for the incompressible D3Q19 model
+    const T inv = M::Q == 19 ? T(1) : T(1) / (T(1) + rl);
+    ux = jx * inv;
+    uy = jy * inv;
+    uz = jz * inv;
+  }
   if (!valid) return;
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     const int q = r + kBCLanes * j;
     if (q >= Q) continue;
     const Lane<T, Q> ln(q);
-    if (ln.x == 1) lane_store(dst + q * kCells, ln, lane_feq<M>(rl, ux, uy, uz, ln));
+    if (!outlet && ln.x == 1) lane_store(dst + q * kCells, ln, lane_feq<M>(rl, ux, uy, uz, ln));
+    // f_eq(rho_out, u_N) + f_N - f_eq(rho_N, u_N) for the populations pulled
+    // into the domain (e_x = -1)
+    if (outlet && ln.x == -1)
+      lane_store(dst + q * kCells, ln,
+                 gs[j] + (lane_feq<M>(T(a.rl_out), ux, uy, uz, ln) - lane_feq<M>(rl, ux, uy, uz, ln)));
   }
 }
 

@@ -102,8 +102,8 @@ struct F2CItem {
 struct BCItem {
   int32_t gblock;
   int16_t gcell;
-  int8_t type;  // 0 inflow (x = -1); only the populations pulled into the
-                // domain (e_x = +1) are written
+  int8_t type;  // 0 inflow (x = -1): the populations with e_x = +1 are
+                // written; 1 pressure outlet (x = NX): those with e_x = -1
   int8_t pad;
   int32_t sblock;
   int16_t scell;
@@ -171,6 +171,7 @@ struct BCArgs {
   const long long* step;  // device coarse-step counter
   double y0, z0, r2, u_in, perturb;
   unsigned long long seed;
+  double rl_out;  // pressure outlet: rho_out - 1 (the density-like value of the storage)
 };
 
 // ------------------------------------------------------------------ launchers

@@ -74,6 +74,8 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
   if (!(omega > 0.0 && omega < 2.0)) return "omega must be in (0, 2)";
   if ((g.walls & 3) % 3 != 0 || (g.walls & 12) % 12 != 0 || (g.walls & ~15) || (g.slip & ~g.walls))
     return "walls come in pairs per axis (bits 0|1 for y, 2|3 for z); slip must be a subset of walls";
+  if (g.outlet != 0 && g.outlet != 1) return "outlet must be 0 (zero-gradient) or 1 (fixed pressure)";
+  if (g.outlet && g.periodic_x) return "a pressure outlet needs a non-periodic x axis";
   const int L = g.levels;
   const int64_t top = int64_t(g.nbx) * g.nby * g.nbz << (3 * (L - 1));
   if (int64_t(g.nbx) << (L - 1) > (1 << 20) || int64_t(g.nby) << (L - 1) > (1 << 20) ||
@@ -88,6 +90,7 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
   P.periodic_x = g.periodic_x != 0;
   P.walls = g.walls;
   P.slip = g.slip;
+  P.outlet = g.outlet;
   const bool px = P.periodic_x;
 
   // ---------------------------------------------------------------- levels
@@ -124,6 +127,14 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
                 snprintf(msg, sizeof msg, "refined block (%d,%d,%d) touches a wall face", bx, by, bz);
                 return msg;
               }
+      }
+      if (l == 0 && g.outlet) {  // and away from the pressure outlet
+        for (int bz = 0; bz < d.nbz; ++bz)
+          for (int by = 0; by < d.nby; ++by)
+            if (d.refined[d.at(d.nbx - 1, by, bz)]) {
+              snprintf(msg, sizeof msg, "refined block (%d,%d,%d) touches the pressure outlet", d.nbx - 1, by, bz);
+              return msg;
+            }
       }
       if (cnt == 0) {
         snprintf(msg, sizeof msg, "level %d refines no block", l);
@@ -269,7 +280,7 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
           w.edges = uint8_t((lp.wrap[0] && X == 0 ? 1 : 0) | (lp.wrap[0] && X == lp.BX - 1 ? 2 : 0) |
                             (lp.wrap[1] && Y == 0 ? 4 : 0) | (lp.wrap[1] && Y == lp.BY - 1 ? 8 : 0) |
                             (lp.wrap[2] && Z == 0 ? 16 : 0) | (lp.wrap[2] && Z == lp.BZ - 1 ? 32 : 0) |
-                            (!px && bx == d.nbx - 1 ? 64 : 0));
+                            (!px && !P.outlet && bx == d.nbx - 1 ? 64 : 0));
           if (!d.refined[i]) {
             std::fill(k, k + 512, uint8_t(K_ACTIVE));
             lp.active_cells += 512;
@@ -354,6 +365,35 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
               else lp.bc.push_back(it);
             }
         }
+      // pressure-outlet ghost column x = NX (refined blocks keep away from
+      // it, so its sources are active cells)
+      if (P.outlet)
+        for (int bz = 0; bz < d.nbz; ++bz)
+          for (int by = 0; by < d.nby; ++by) {
+            if (!bch[by + int64_t(d.nby) * bz]) continue;
+            const int32_t gb = lp.box_id(d.nbx, by, bz);
+            const int32_t sb = lp.box_id(d.nbx - 1, by, bz);
+            if (gb < 0) return "internal: boundary block outside its box";
+            if (sb < 0) continue;
+            for (int cz = 0; cz < 8; ++cz)
+              for (int cy = 0; cy < 8; ++cy) {
+                const int sc = 7 + 8 * cy + 64 * cz;
+                if (lp.kind[int64_t(sb) * 512 + sc] == K_NONE) continue;
+                if (lp.kind[int64_t(sb) * 512 + sc] == K_GHOST) return "internal: outlet source is a ghost cell";
+                const int gc = 8 * cy + 64 * cz;
+                lp.kind[int64_t(gb) * 512 + gc] = K_BC;
+                lp.bc_cells++;
+                BCItem it{};
+                it.gblock = gb;
+                it.gcell = int16_t(gc);
+                it.type = 1;
+                it.sblock = sb;
+                it.scell = int16_t(sc);
+                it.y = 8 * by + cy;
+                it.z = 8 * bz + cz;
+                lp.bc.push_back(it);
+              }
+          }
     }
     (void)box_of;
   }

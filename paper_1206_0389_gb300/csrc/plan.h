@@ -49,6 +49,7 @@ struct GridPlan {
   int levels = 1;
   bool periodic_x = true;
   int walls = 0, slip = 0;  // level-0 wall faces (bit 0/1 low/high y, 2/3 low/high z), free-slip subset
+  int outlet = 0;           // 1: pressure outlet on x = NX (level 0)
   std::vector<LevelPlan> lv;
   int64_t device_bytes = 0;
 };

@@ -19,7 +19,8 @@ LBM_F64, LBM_F32, LBM_F16 = 0, 1, 2
 LBM_MAX_LEVELS = 4
 MODELS = {"d3q19": LBM_D3Q19_MRT_LES, "d3q27": LBM_D3Q27_FCLB}
 STORAGES = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16}
-EXPORTED = ["lbm_plan", "lbm_create", "lbm_create_error", "lbm_set_inflow", "lbm_init_equilibrium",
+EXPORTED = ["lbm_plan", "lbm_create", "lbm_create_error", "lbm_set_inflow", "lbm_set_outlet",
+            "lbm_init_equilibrium",
             "lbm_set_force", "lbm_step", "lbm_sync", "lbm_macroscopic", "lbm_mass_momentum",
             "lbm_get_state", "lbm_set_state", "lbm_get_cells", "lbm_get_step", "lbm_set_step",
             "lbm_set_profiling", "lbm_get_profile", "lbm_get_tuning", "lbm_last_error", "lbm_destroy",
@@ -37,7 +38,8 @@ class LbmError(RuntimeError):
 
 class lbm_grid(ctypes.Structure):
     _fields_ = [("nbx", c_int), ("nby", c_int), ("nbz", c_int), ("periodic_x", c_int),
-                ("levels", c_int), ("refine", POINTER(c_uint8)), ("walls", c_int), ("slip", c_int)]
+                ("levels", c_int), ("refine", POINTER(c_uint8)), ("walls", c_int), ("slip", c_int),
+                ("outlet", c_int)]
 
 
 class lbm_plan_info(ctypes.Structure):
@@ -65,6 +67,7 @@ def load():
         "lbm_create": (c_int, [P(c_void_p), c_int, c_int, P(lbm_grid), c_double, c_double, c_void_p]),
         "lbm_create_error": (c_char_p, []),
         "lbm_set_inflow": (c_int, [c_void_p, c_double, c_double, c_double, c_double, c_double, c_uint64]),
+        "lbm_set_outlet": (c_int, [c_void_p, c_double]),
         "lbm_init_equilibrium": (c_int, [c_void_p, c_int, D, D]),
         "lbm_set_force": (c_int, [c_void_p, D]),
         "lbm_step": (c_int, [c_void_p, c_int]),
@@ -109,21 +112,21 @@ def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
 
 
-def make_grid(nb, periodic_x=True, refine=(), walls=0, slip=0):
+def make_grid(nb, periodic_x=True, refine=(), walls=0, slip=0, outlet=0):
     """lbm_grid from coarse block counts nb = (nbx, nby, nbz), refine flags
-    (list of arrays shaped (nbz*2^l, nby*2^l, nbx*2^l)) and the wall faces
-    (bit 0/1 low/high y, 2/3 low/high z; slip the free-slip subset).
-    Returns (grid, keepalive)."""
+    (list of arrays shaped (nbz*2^l, nby*2^l, nbx*2^l)), the wall faces
+    (bit 0/1 low/high y, 2/3 low/high z; slip the free-slip subset) and the
+    outlet type (0 zero-gradient, 1 fixed pressure).  Returns (grid, keepalive)."""
     flags = [np.ascontiguousarray(np.asarray(r, dtype=np.uint8)).reshape(-1) for r in refine]
     buf = np.concatenate(flags) if flags else np.zeros(1, dtype=np.uint8)
     g = lbm_grid(int(nb[0]), int(nb[1]), int(nb[2]), 1 if periodic_x else 0, len(flags) + 1,
-                 buf.ctypes.data_as(POINTER(c_uint8)), int(walls), int(slip))
+                 buf.ctypes.data_as(POINTER(c_uint8)), int(walls), int(slip), int(outlet))
     return g, buf
 
 
-def lbm_plan(nb, periodic_x=True, refine=(), model="d3q19", storage="f32", walls=0, slip=0):
+def lbm_plan(nb, periodic_x=True, refine=(), model="d3q19", storage="f32", walls=0, slip=0, outlet=0):
     lib = load()
-    g, keep = make_grid(nb, periodic_x, refine, walls, slip)
+    g, keep = make_grid(nb, periodic_x, refine, walls, slip, outlet)
     info = lbm_plan_info()
     st = lib.lbm_plan(ctypes.byref(g), MODELS[model], STORAGES[storage], ctypes.byref(info))
     if st != LBM_OK:
@@ -157,9 +160,9 @@ def _check(ctx, st):
 
 
 def lbm_create(model, storage, nb, periodic_x=True, refine=(), omega=1.0, cs=0.0, stream=None,
-               walls=0, slip=0):
+               walls=0, slip=0, outlet=0):
     lib = load()
-    g, keep = make_grid(nb, periodic_x, refine, walls, slip)
+    g, keep = make_grid(nb, periodic_x, refine, walls, slip, outlet)
     h = c_void_p()
     st = lib.lbm_create(ctypes.byref(h), MODELS[model], STORAGES[storage], ctypes.byref(g),
                         float(omega), float(cs), stream)
@@ -176,6 +179,10 @@ def lbm_destroy(ctx):
 
 def lbm_set_inflow(ctx, y0, z0, diameter, u_in, perturb=0.01, seed=0):
     _check(ctx, load().lbm_set_inflow(ctx.h, y0, z0, diameter, u_in, perturb, int(seed)))
+
+
+def lbm_set_outlet(ctx, rho_out):
+    _check(ctx, load().lbm_set_outlet(ctx.h, float(rho_out)))
 
 
 def lbm_init_equilibrium(ctx, level, rho=None, u=None):

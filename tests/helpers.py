@@ -14,13 +14,14 @@ def gpu():
     return lbm
 
 
-def make_pair(model, storage, nb, periodic_x=True, refine=(), omega=1.6, cs=0.0, walls=0, slip=0):
+def make_pair(model, storage, nb, periodic_x=True, refine=(), omega=1.6, cs=0.0, walls=0, slip=0,
+              outlet=0):
     lbm = gpu()
     ctx = lbm.lbm_create(model, storage, nb, periodic_x, [np.asarray(r) for r in refine], omega, cs,
-                         walls=walls, slip=slip)
+                         walls=walls, slip=slip, outlet=outlet)
     orc = NestedSolver(model, nb, periodic_x=periodic_x,
                        refine=[torch.as_tensor(np.asarray(r)).bool() for r in refine],
-                       omega=omega, cs=cs, walls=walls, slip=slip)
+                       omega=omega, cs=cs, walls=walls, slip=slip, outlet=outlet)
     return ctx, orc
 
 

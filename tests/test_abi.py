@@ -137,6 +137,30 @@ def test_plan_rejects_refinement_next_to_walls():
         lbm.lbm_plan((4, 3, 3), False, [r2], walls=15 - bad_wall)
 
 
+def test_plan_outlet_rules_match_oracle():
+    """The pressure outlet needs a non-periodic x axis and keeps refined blocks
+    one block away from its face; its ghost column doubles the level-0
+    boundary cells."""
+    r = np.zeros((2, 2, 3), dtype=bool)
+    r[:, :, 0] = True
+    info = lbm.lbm_plan((3, 2, 2), False, [r], outlet=1)
+    plain = lbm.lbm_plan((3, 2, 2), False, [r])
+    assert info.bc_cells[0] == plain.bc_cells[0] + 16 * 16
+    NestedSolver("d3q27", (3, 2, 2), periodic_x=False, refine=[torch.from_numpy(r)], outlet=1)
+    bad = np.zeros((2, 2, 3), dtype=bool)
+    bad[:, :, 2] = True
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_plan((3, 2, 2), False, [bad], outlet=1)
+    with pytest.raises(ValueError):
+        NestedSolver("d3q27", (3, 2, 2), periodic_x=False, refine=[torch.from_numpy(bad)], outlet=1)
+    lbm.lbm_plan((3, 2, 2), False, [bad])            # fine with the zero-gradient outflow
+    for bad_args in (dict(periodic_x=True, outlet=1), dict(periodic_x=False, outlet=2)):
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_plan((3, 2, 2), bad_args["periodic_x"], [], outlet=bad_args["outlet"])
+        with pytest.raises(ValueError):
+            NestedSolver("d3q27", (3, 2, 2), **bad_args)
+
+
 def test_create_without_gpu_reports_cuda_error():
     if torch.cuda.is_available():
         pytest.skip("a GPU is present")
