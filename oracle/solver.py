@@ -65,16 +65,20 @@ import torch
 from . import DTYPE
 from .collision import Model
 from .grid import build_levels
+from .nozzle import Body, Cylinder, nozzle_level
 from .rng import inflow_xi
 
 
 class NestedSolver:
     def __init__(self, model, nb, periodic_x=True, refine=(), omega=1.0, cs=0.0, walls=0, slip=0,
-                 outlet=0):
+                 outlet=0, nozzle=None, body=None):
         """walls: bit 0/1 the low/high y face, bit 2/3 the low/high z face are
         walls (both faces of an axis or neither); slip: the same bits mark the
         free-slip walls among them (the others are no-slip).  outlet: 0
-        zero-gradient outflow, 1 fixed-pressure outlet (non-periodic x)."""
+        zero-gradient outflow, 1 fixed-pressure outlet (non-periodic x).
+        nozzle: (y0, z0, R, x0, x1) of the nozzle cylinder (oracle/nozzle.py),
+        or None; body: another geometry of oracle/nozzle.py on a single-level
+        grid (the pins' plane walls)."""
         self.m = Model(model)
         self.Q = self.m.Q
         if (walls & 3) not in (0, 3) or (walls & 12) not in (0, 12) or (walls & ~15) or (slip & ~walls):
@@ -98,6 +102,19 @@ class NestedSolver:
                 raise ValueError("refined blocks must keep one block away from the walls")
         self.levels = build_levels(nb, periodic_x, refine)
         self.L = len(self.levels)
+        self.body, self.nozzle = None, nozzle is not None
+        if nozzle is not None or body is not None:
+            if nozzle is not None:
+                geom = Cylinder(*nozzle)
+                ln = nozzle_level(self.levels, geom)
+            else:
+                if self.L != 1:
+                    raise ValueError("a test body needs a single-level grid")
+                geom, ln = body, 0
+            self.body = Body(geom, self.levels[ln], ln, self.m.e, periodic_x)
+            lv = self.levels[ln]
+            for name in ("active", "update", "valid"):
+                setattr(lv, name, getattr(lv, name) & ~self.body.solid)
         self.periodic_x = periodic_x
         self.omega0 = float(omega)
         self.cs = float(cs) if model == "d3q19" else 0.0
@@ -188,6 +205,8 @@ class NestedSolver:
                              p["u_in"] * p["perturb"] * xi[1],
                              p["u_in"] * p["perturb"] * xi[2]])
             u = torch.where(inside[None], u, torch.zeros_like(u))
+            if self.nozzle:                  # the inflow sits on the nozzle's cap
+                u = torch.zeros_like(u)
             f[:, zz, yy, 0] = self.m.feq(rl, u)
         # outflow column x = NX (index NX+1) from cell x = NX-1 (index NX):
         # a copy (zero gradient), or at the pressure outlet the equilibrium at
@@ -196,6 +215,36 @@ class NestedSolver:
         if len(zz):
             src = f[:, zz, yy, lv.NX]
             f[:, zz, yy, lv.NX + 1] = self._outlet_ghost(src) if self.outlet else src
+
+    def _body_links(self, l, sub):
+        """Populations of the solid cells that the body's links pull
+        (oracle/nozzle.py): interpolated no-slip values, and on the nozzle's
+        cap the inflow equilibrium from the fluid cell straight downstream."""
+        b = self.body
+        if b is None or l != b.l or len(b.i) == 0:
+            return
+        f = self.f[l]
+        val = b.wall_values(f)
+        if bool(b.inflow.any()):
+            lv = self.levels[l]
+            k = torch.nonzero(b.inflow, as_tuple=True)[0]
+            bz, by, bx = (idx[k] for idx in b.b_idx)
+            down = f[:, bz, by, bx + 1]
+            rl = self.m.density_like(down)
+            p = self.inflow
+            sc = 1.0 / (2 ** l)
+            yc = (by.to(DTYPE) + 0.5) * sc
+            zc = (bz.to(DTYPE) + 0.5) * sc
+            inside = (yc - p["y0"]) ** 2 + (zc - p["z0"]) ** 2 < (0.5 * p["D"]) ** 2
+            cell = (by + lv.NY * bz).numpy()
+            xi = [torch.from_numpy(inflow_xi(p["seed"], self.coarse_step, l, sub, cell, c)) for c in range(3)]
+            u = torch.stack([p["u_in"] * (1.0 + p["perturb"] * xi[0]),
+                             p["u_in"] * p["perturb"] * xi[1],
+                             p["u_in"] * p["perturb"] * xi[2]])
+            u = torch.where(inside[None], u, torch.zeros_like(u))
+            feq = self.m.feq(rl, u)
+            val[k] = feq[b.ib[k], torch.arange(len(k))]
+        f[b.ib, b.b_idx[0], b.b_idx[1], b.b_idx[2]] = val
 
     def _outlet_ghost(self, src):
         """Pressure-outlet ghosts from the cells x = NX - 1 (Q, n): the
@@ -340,6 +389,7 @@ class NestedSolver:
 
     def _advance(self, l, sub):
         self._apply_bc(l, sub)
+        self._body_links(l, sub)
         old, oldS = self.f[l].clone(), self.S[l].clone()
         new, newS = self._update(l)
         if l + 1 < self.L:

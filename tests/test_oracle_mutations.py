@@ -199,3 +199,56 @@ def test_outlet_with_the_density_correction_reversed_is_caught(monkeypatch):
     _plant_outlet(monkeypatch, ghost)
     assert fails(TO.test_outlet_ghost_has_outlet_density_and_cell_velocity, "d3q19")
     assert fails(TO.test_outlet_drains_overpressure_to_rho_out, "d3q27")
+
+
+def test_bouzidi_with_q_fixed_at_one_half_is_caught(monkeypatch):
+    """Interpolated walls treated as half-way bounce-back (q ignored)."""
+    from oracle import nozzle as N
+    from tests import test_oracle_nozzle as TZ
+    orig = N.Body.wall_values
+
+    def wall_values(self, f):
+        q = self.q
+        self.q = torch.full_like(q, 0.5)
+        try:
+            return orig(self, f)
+        finally:
+            self.q = q
+    monkeypatch.setattr(N.Body, "wall_values", wall_values)
+    assert fails(TZ.test_plane_walls_at_any_position_hold_poiseuille, 2.3, 5.2)
+
+
+def test_bouzidi_with_one_branch_for_all_q_is_caught(monkeypatch):
+    """The q < 1/2 interpolation used for every link (an extrapolation for
+    q > 1/2)."""
+    from oracle import nozzle as N
+    from tests import test_oracle_nozzle as TZ
+
+    def wall_values(self, f):
+        a = f[self.i, self.f_idx[0], self.f_idx[1], self.f_idx[2]]
+        b = f[self.i, self.s_idx[0], self.s_idx[1], self.s_idx[2]]
+        return torch.where(self.has2, 2.0 * self.q * a + (1.0 - 2.0 * self.q) * b, a)
+    monkeypatch.setattr(N.Body, "wall_values", wall_values)
+    assert fails(TZ.test_plane_walls_at_any_position_hold_poiseuille, 2.3, 5.2)
+
+
+def test_cap_inflow_with_the_wrong_density_cell_is_caught(monkeypatch):
+    """The cap's inflow equilibrium taking the density of the solid cell
+    instead of the fluid cell downstream."""
+    from tests import test_oracle_nozzle as TZ
+    orig = S.NestedSolver._body_links
+
+    def links(self, l, sub):
+        b = self.body
+        if b is None:
+            return orig(self, l, sub)
+        keep = b.b_idx
+        f = self.f[l]
+        # shift the index the cap rule adds one to: reads x_b itself
+        b.b_idx = (keep[0], keep[1], keep[2] - b.inflow.long())
+        try:
+            orig(self, l, sub)
+        finally:
+            b.b_idx = keep
+    monkeypatch.setattr(S.NestedSolver, "_body_links", links)
+    assert fails(TZ.test_cap_inflow_equals_face_inflow, "d3q27")
