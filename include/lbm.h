@@ -88,7 +88,23 @@ typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2 } lbm_storage;
  * equilibrium at the outlet density (lbm_set_outlet; 1 until called) with
  * the velocity of the cell x = NX - 1 plus that cell's non-equilibrium part,
  * f_ghost = f_eq(rho_out, u_N) + f_N - f_eq(rho_N, u_N).  Refined level-0
- * blocks must keep one block away from that face (checked). */
+ * blocks must keep one block away from that face (checked).
+ *
+ * Nozzle (Section 3.2: a cylinder along the jet axis with second-order
+ * interpolated no-slip walls after Bouzidi et al.; its downstream end emits
+ * the jet): nozzle_r > 0 makes the closed cylinder x0 <= x <= x1,
+ * (y - y0)^2 + (z - z0)^2 <= r^2 (coarse-cell units; cells whose centre lies
+ * in it) solid.  Its surface is a no-slip wall by Bouzidi's linear
+ * interpolation: a link from fluid cell f to solid cell f + e_i cut at the
+ * fraction q takes 2q f~_i(f) + (1 - 2q) f~_i(f - e_i) for q < 1/2
+ * (f~_i(f) if f - e_i is solid) and f~_i(f)/(2q) + (2q - 1)/(2q) f~_ib(f)
+ * otherwise.  Links that enter through the downstream cap x = x1 carry the
+ * inflow instead: the disc inflow of lbm_set_inflow moves from the face
+ * x = 0 onto the cap (the solid cell takes f_eq(rho of the fluid cell
+ * downstream, u_bc at its own y, z)) and the face x = 0 holds u = 0.  The
+ * body lives on one level: the finest whose blocks cover the cylinder grown
+ * by two of its cells, each of them a non-refined block whose 26 neighbours
+ * are blocks of that level (checked; lbm_plan_info.nozzle_level). */
 typedef struct {
   int nbx, nby, nbz;
   int periodic_x;
@@ -97,6 +113,7 @@ typedef struct {
   int walls; /* wall faces, see above; 0 = periodic y and z */
   int slip;  /* free-slip subset of walls */
   int outlet; /* 0 zero-gradient outflow, 1 fixed-pressure outlet */
+  double nozzle_y0, nozzle_z0, nozzle_r, nozzle_x0, nozzle_x1; /* nozzle_r <= 0: none */
 } lbm_grid;
 
 /* Sizes of a grid, computed on the host without touching a GPU. */
@@ -113,6 +130,9 @@ typedef struct {
   int64_t updates_per_coarse_step;       /* sum_l updated_cells[l] * 2^l            */
   int64_t active_updates_per_coarse_step;/* sum_l active_cells[l] * 2^l             */
   int64_t device_bytes;                  /* device memory lbm_create would allocate */
+  int nozzle_level;                      /* level holding the nozzle, -1 if none    */
+  int64_t solid_cells;                   /* cells inside the nozzle                 */
+  int64_t nozzle_links;                  /* links of its surface and cap            */
 } lbm_plan_info;
 
 /* Plan a grid on the host (no CUDA call).  Validates g like lbm_create.

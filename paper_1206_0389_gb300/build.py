@@ -33,7 +33,10 @@ def _compile(src):
                "-Xptxas", "-v", "-c", path, "-o", obj]
 
     else:
-        cmd = [nvcc(), "-std=c++17", "-O2", "-x", "c++", "-Xcompiler", "-fPIC", "-c", path, "-o", obj]
+        # no contraction of a*b + c: the planner's geometry (nozzle cells and
+        # link fractions) rounds the same on every host
+        cmd = [nvcc(), "-std=c++17", "-O2", "-x", "c++", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+               "-c", path, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("compile failed: %s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))

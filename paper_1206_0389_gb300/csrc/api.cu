@@ -30,11 +30,12 @@ namespace {
 thread_local std::string g_create_error;
 
 struct Op {
-  enum Kind { UPDATE, C2F, F2C, BC, INC } kind;
+  enum Kind { UPDATE, C2F, F2C, BC, LINK, INC } kind;
   UpdateArgs ua{};
   C2FArgs ca{};
   F2CArgs fa{};
   BCArgs ba{};
+  LinkArgs la{};
 };
 
 struct DevLevel {
@@ -47,6 +48,7 @@ struct DevLevel {
   BCItem* c2f_bc = nullptr;
   F2CItem* f2c = nullptr;
   BCItem* bc = nullptr;
+  LinkItem* links = nullptr;
   double* force = nullptr;
   float* force_f = nullptr;  // float copy for FP32/FP16 storage (compute type)
   double* stats = nullptr;   // time statistics sums [7][nblocks*512]
@@ -143,6 +145,7 @@ void free_all(lbm_ctx* c) {
     cudaFree(d.c2f_bc);
     cudaFree(d.f2c);
     cudaFree(d.bc);
+    cudaFree(d.links);
     cudaFree(d.force);
     cudaFree(d.force_f);
     cudaFree(d.stats);
@@ -195,6 +198,7 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
       a.u_in = c->u_in;
       a.perturb = c->perturb;
       a.seed = c->seed;
+      a.closed = c->plan.nozzle_level >= 0;
       for (int l = std::max(lmin, 1); l < L; ++l) {
         const int s = sub(l) % 2;
         const LevelPlan& fp = c->plan.lv[l];
@@ -238,6 +242,7 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
       b.perturb = c->perturb;
       b.seed = c->seed;
       b.rl_out = c->rho_out - 1.0;
+      b.closed = c->plan.nozzle_level >= 0;
       for (int l = lmin; l < L; ++l) {
         const LevelPlan& lp = c->plan.lv[l];
         if (lp.bc.empty()) continue;
@@ -252,6 +257,29 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
         b.n += v.n;
       }
       if (b.n > 0) ops.push_back(op);
+    }
+    // nozzle links of its level (after the level's previous update, before
+    // this one; they touch only cells near the body)
+    const int ln = c->plan.nozzle_level;
+    if (ln >= lmin && !c->plan.lv[ln].links.empty()) {
+      Op op;
+      op.kind = Op::LINK;
+      LinkArgs& a = op.la;
+      a.items = c->dl[ln].links;
+      a.n = int(c->plan.lv[ln].links.size());
+      a.f = c->dl[ln].f[par[ln]];
+      a.level = ln;
+      a.substep = sub(ln);
+      a.NY = c->plan.lv[ln].NY;
+      a.inv_scale = std::ldexp(1.0, -ln);
+      a.step = c->d_step;
+      a.y0 = c->y0;
+      a.z0 = c->z0;
+      a.r2 = (0.5 * c->diameter) * (0.5 * c->diameter);
+      a.u_in = c->u_in;
+      a.perturb = c->perturb;
+      a.seed = c->seed;
+      ops.push_back(op);
     }
     Op up;
     up.kind = Op::UPDATE;
@@ -316,6 +344,7 @@ cudaError_t run_op(lbm_ctx* c, const Op& op, cudaStream_t st) {
     case Op::C2F: return launch_c2f(c->model, c->storage, op.ca, st);
     case Op::F2C: return launch_f2c(c->model, c->storage, op.fa, st);
     case Op::BC: return launch_bc(c->model, c->storage, op.ba, st);
+    case Op::LINK: return launch_links(c->model, c->storage, op.la, st);
     case Op::INC: return launch_step_inc(c->d_step, st);
   }
   return cudaErrorInvalidValue;
@@ -327,7 +356,8 @@ int op_kind_index(const Op& op) {
     case Op::UPDATE: return 0;
     case Op::C2F: return 1;
     case Op::F2C: return 2;
-    case Op::BC: return 3;
+    case Op::BC:
+    case Op::LINK: return 3;
     default: return 4;
   }
 }
@@ -568,6 +598,9 @@ int lbm_plan(const lbm_grid* g, int model, int storage, lbm_plan_info* out) {
     out->active_updates_per_coarse_step += lp.active_cells << l;
   }
   out->device_bytes = P.device_bytes;
+  out->nozzle_level = P.nozzle_level;
+  out->solid_cells = P.nozzle_level >= 0 ? P.lv[P.nozzle_level].solid_cells : 0;
+  out->nozzle_links = P.nozzle_level >= 0 ? int64_t(P.lv[P.nozzle_level].links.size()) : 0;
   return LBM_OK;
 }
 
@@ -658,7 +691,8 @@ int lbm_create(lbm_ctx** out, lbm_model model, lbm_storage storage, const lbm_gr
         (ce = upload(&d.c2f_chunks, lp.c2f_chunks)) != cudaSuccess ||
         (ce = upload(&d.c2f_cells, lp.c2f_cells)) != cudaSuccess ||
         (ce = upload(&d.c2f_bc, lp.c2f_bc)) != cudaSuccess ||
-        (ce = upload(&d.f2c, lp.f2c)) != cudaSuccess || (ce = upload(&d.bc, lp.bc)) != cudaSuccess)
+        (ce = upload(&d.f2c, lp.f2c)) != cudaSuccess || (ce = upload(&d.bc, lp.bc)) != cudaSuccess ||
+        (ce = upload(&d.links, lp.links)) != cudaSuccess)
       return bail(LBM_ERR_OOM, std::string("plan tables: ") + cudaGetErrorString(ce));
     const int16_t moff = int16_t(masks.size() / 16);
     masks.insert(masks.end(), lp.masks.begin(), lp.masks.end());
@@ -1078,7 +1112,8 @@ int lbm_adjoint_forward(lbm_ctx* ctx, int T, int checkpoint_every) {
   if (!ctx) return LBM_ERR_ARG;
   if (ctx->model != LBM_D3Q27_FCLB || ctx->L != 1 || !ctx->plan.periodic_x)
     return fail(ctx, LBM_ERR_STATE, "the adjoint is defined for single-level periodic D3Q27 grids");
-  if (ctx->plan.walls) return fail(ctx, LBM_ERR_STATE, "the adjoint is defined without walls");
+  if (ctx->plan.walls || ctx->plan.nozzle_level >= 0)
+    return fail(ctx, LBM_ERR_STATE, "the adjoint is defined without walls or a nozzle");
   if (ctx->storage == LBM_F16) return fail(ctx, LBM_ERR_STATE, "the adjoint needs F32 or F64 storage");
   if (T < 1 || checkpoint_every < 1 || checkpoint_every > T)
     return fail(ctx, LBM_ERR_ARG, "need T >= 1 and 1 <= checkpoint_every <= T");

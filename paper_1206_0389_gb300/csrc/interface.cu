@@ -243,8 +243,9 @@ __global__ void __launch_bounds__(kC2FMaxItems) k_c2f(const C2FArgs a) {
     T ub[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      ub[c] = T(inflow_u(a.step, a.y0, a.z0, a.r2, a.u_in, a.perturb, a.seed, L.level, L.substep, L.NY,
-                         L.inv_scale, b.y, b.z, c));
+      ub[c] = a.closed ? T(0)
+                       : T(inflow_u(a.step, a.y0, a.z0, a.r2, a.u_in, a.perturb, a.seed, L.level, L.substep,
+                                    L.NY, L.inv_scale, b.y, b.z, c));
     T fb[Q];
     M::feq(rl, ub[0], ub[1], ub[2], fb);
     S* gd = reinterpret_cast<S*>(L.f_dst) + int64_t(b.gblock) * QS + b.gcell;
@@ -373,7 +374,7 @@ __global__ void __launch_bounds__(128) k_bc(const BCArgs a) {
   // scarce on this part.  Every lane takes part in the shuffles (groups of
   // both item types may share a warp).
   T uc = T(0);
-  if (it.type == 0 && r < 3)
+  if (it.type == 0 && r < 3 && !a.closed)
     uc = T(inflow_u(a.step, a.y0, a.z0, a.r2, a.u_in, a.perturb, a.seed, L.level, L.substep, L.NY, L.inv_scale,
                     it.y, it.z, r));
   const int g0 = int(threadIdx.x & 31) & ~(kBCLanes - 1);
@@ -404,6 +405,52 @@ __global__ void __launch_bounds__(128) k_bc(const BCArgs a) {
   }
 }
 
+// Nozzle links (LinkItem): one thread per link.  The value is written into
+// population ib of the solid cell, where the pull of the fluid cell takes it.
+// Bouzidi linear interpolation (no-slip at fraction q of the link):
+//   q <  1/2: 2q f~_i(f) + (1 - 2q) f~_i(f - e_i)   (f~_i(f) if f - e_i is solid)
+//   q >= 1/2: f~_i(f) / (2q) + (2q - 1)/(2q) f~_ib(f)
+// Both are affine with weights summing to 1 and w_i = w_ib, so they apply to
+// the shifted storage values unchanged.  On the downstream cap: the inflow
+// equilibrium with the density of the fluid cell straight downstream.
+template <class M, class S>
+__global__ void __launch_bounds__(128) k_links(const LinkArgs a) {
+  using T = typename Store<S>::T;
+  constexpr int Q = M::Q;
+  constexpr int QS = Q * kCells;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.n) return;
+  const LinkItem it = a.items[t];
+  S* f = reinterpret_cast<S*>(a.f);
+  const int i = it.i, ib = it.ib;
+  T v;
+  if (it.type == 0) {
+    const T q = T(it.q);
+    const T fi = load_rt<S, Q>(f + int64_t(it.fblock) * QS + i * kCells + it.fcell, i);
+    if (it.q < 0.5) {
+      v = fi;
+      if (it.sblock >= 0) {
+        const T si = load_rt<S, Q>(f + int64_t(it.sblock) * QS + i * kCells + it.scell, i);
+        v = T(2) * q * fi + (T(1) - T(2) * q) * si;
+      }
+    } else {
+      const T fb = load_rt<S, Q>(f + int64_t(it.fblock) * QS + ib * kCells + it.fcell, ib);
+      v = fi / (T(2) * q) + (T(2) * q - T(1)) / (T(2) * q) * fb;
+    }
+  } else {
+    const S* s = f + int64_t(it.sblock) * QS + it.scell;
+    T rl = T(0);
+    for (int k = 0; k < Q; ++k) rl += load_rt<S, Q>(s + k * kCells, k);
+    T u[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      u[c] = T(inflow_u(a.step, a.y0, a.z0, a.r2, a.u_in, a.perturb, a.seed, a.level, a.substep, a.NY, a.inv_scale,
+                        it.y, it.z, c));
+    v = lane_feq<M>(rl, u[0], u[1], u[2], Lane<T, Q>(ib));
+  }
+  store_rt<S, Q>(f + int64_t(it.bblock) * QS + ib * kCells + it.bcell, ib, v);
+}
+
 __global__ void k_step_inc(long long* step) { *step += 1; }
 
 // coarse-to-fine: one CTA per chunk; fine-to-coarse: four lanes per item, 32
@@ -418,6 +465,12 @@ template <class M, class S>
 static cudaError_t f2c_ms(const F2CArgs& a, cudaStream_t st) {
   if (a.n == 0) return cudaSuccess;
   k_f2c<M, S><<<(a.n + 31) / 32, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+template <class M, class S>
+static cudaError_t links_ms(const LinkArgs& a, cudaStream_t st) {
+  if (a.n == 0) return cudaSuccess;
+  k_links<M, S><<<(a.n + 127) / 128, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 template <class M, class S>
@@ -440,6 +493,7 @@ static cudaError_t bc_ms(const BCArgs& a, cudaStream_t st) {
 cudaError_t launch_c2f(int model, int storage, const C2FArgs& a, cudaStream_t st) { LBM_DISPATCH(c2f_ms, a, st) }
 cudaError_t launch_f2c(int model, int storage, const F2CArgs& a, cudaStream_t st) { LBM_DISPATCH(f2c_ms, a, st) }
 cudaError_t launch_bc(int model, int storage, const BCArgs& a, cudaStream_t st) { LBM_DISPATCH(bc_ms, a, st) }
+cudaError_t launch_links(int model, int storage, const LinkArgs& a, cudaStream_t st) { LBM_DISPATCH(links_ms, a, st) }
 
 cudaError_t launch_step_inc(long long* step, cudaStream_t st) {
   k_step_inc<<<1, 1, 0, st>>>(step);

@@ -32,7 +32,8 @@ enum CellKind : uint8_t {
   K_HIDDEN2 = 3,  // refined, distance 2
   K_REFINED = 4,  // refined, deeper inside
   K_GHOST = 5,    // coarse-to-fine ghost cell
-  K_BC = 6        // inflow/outflow ghost cell
+  K_BC = 6,       // inflow/outflow ghost cell
+  K_SOLID = 7     // inside the nozzle (not updated; its link populations are set)
 };
 
 struct LevelPtrs {
@@ -139,6 +140,7 @@ struct C2FArgs {
   const long long* step;  // inflow (see BCArgs)
   double y0, z0, r2, u_in, perturb;
   unsigned long long seed;
+  int closed;             // the face inflow holds u = 0 (the inflow sits on the nozzle's cap)
 };
 
 struct F2CLevel {
@@ -172,6 +174,34 @@ struct BCArgs {
   double y0, z0, r2, u_in, perturb;
   unsigned long long seed;
   double rl_out;  // pressure outlet: rho_out - 1 (the density-like value of the storage)
+  int closed;     // the face inflow holds u = 0 (the inflow sits on the nozzle's cap)
+};
+
+// a link of the nozzle's surface: fluid cell f, direction i towards the solid
+// cell b = f + e_i, ib the opposite direction.  type 0 (no-slip, Bouzidi
+// linear interpolation at fraction q): population ib of b is set from
+// f~_i(f), f~_i(s) with s = f - e_i (sblock < 0: s is solid, half-way
+// bounce-back) and f~_ib(f).  type 1 (on the downstream cap): population ib
+// of b is f_eq(rho(s), u_bc) with s = b + x^ and u_bc the inflow disc
+// velocity at the level-local (y, z) of b.
+struct LinkItem {
+  double q;
+  int32_t fblock, bblock, sblock;
+  int16_t fcell, bcell, scell;
+  uint8_t i, ib;
+  uint8_t type, pad;
+  int16_t pad2;
+  int32_t y, z;
+};
+struct LinkArgs {
+  const LinkItem* items;
+  int n;
+  void* f;  // storage of the nozzle's level at the current time
+  int level, substep, NY;
+  double inv_scale;
+  const long long* step;
+  double y0, z0, r2, u_in, perturb;
+  unsigned long long seed;
 };
 
 // ------------------------------------------------------------------ launchers
@@ -182,6 +212,7 @@ cudaError_t update_occupancy(int model, int storage, bool walls, int threads, in
 cudaError_t launch_c2f(int model, int storage, const C2FArgs& a, cudaStream_t st);
 cudaError_t launch_f2c(int model, int storage, const F2CArgs& a, cudaStream_t st);
 cudaError_t launch_bc(int model, int storage, const BCArgs& a, cudaStream_t st);
+cudaError_t launch_links(int model, int storage, const LinkArgs& a, cudaStream_t st);
 cudaError_t launch_step_inc(long long* step, cudaStream_t st);
 
 // dense <-> block staging for one slab of cell layers [z0, z0 + nz) of a level

@@ -76,6 +76,10 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
     return "walls come in pairs per axis (bits 0|1 for y, 2|3 for z); slip must be a subset of walls";
   if (g.outlet != 0 && g.outlet != 1) return "outlet must be 0 (zero-gradient) or 1 (fixed pressure)";
   if (g.outlet && g.periodic_x) return "a pressure outlet needs a non-periodic x axis";
+  const bool nozzle = g.nozzle_r > 0;
+  if (nozzle && !(std::isfinite(g.nozzle_y0) && std::isfinite(g.nozzle_z0) && std::isfinite(g.nozzle_r) &&
+                  std::isfinite(g.nozzle_x0) && std::isfinite(g.nozzle_x1) && g.nozzle_x0 < g.nozzle_x1))
+    return "nozzle: finite values with x0 < x1 required";
   const int L = g.levels;
   const int64_t top = int64_t(g.nbx) * g.nby * g.nbz << (3 * (L - 1));
   if (int64_t(g.nbx) << (L - 1) > (1 << 20) || int64_t(g.nby) << (L - 1) > (1 << 20) ||
@@ -553,6 +557,163 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
         }
   }
 
+  // ---------------------------------------------------------------- nozzle
+  if (nozzle) {
+    const double y0 = g.nozzle_y0, z0 = g.nozzle_z0, R = g.nozzle_r, x0 = g.nozzle_x0, x1 = g.nozzle_x1;
+    // the finest level whose blocks cover the cylinder grown by two of its
+    // cells, all of them non-refined with their 26 neighbours in the level
+    int ln = -1;
+    double box[3][2];
+    for (int l = L - 1; l >= 0 && ln < 0; --l) {
+      const double sc = std::ldexp(1.0, l);
+      const double b[3][2] = {{x0 * sc - 2, x1 * sc + 2}, {(y0 - R) * sc - 2, (y0 + R) * sc + 2},
+                              {(z0 - R) * sc - 2, (z0 + R) * sc + 2}};
+      const DomainLevel& d = D[l];
+      const int nbs[3] = {d.nbx, d.nby, d.nbz};
+      int lo[3], hi[3];
+      bool ok = true;
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = int(std::floor(b[a][0] / 8));
+        hi[a] = int(std::floor(b[a][1] / 8));
+        ok = ok && lo[a] - 1 >= 0 && hi[a] + 1 <= nbs[a] - 1;
+      }
+      for (int bz = lo[2]; ok && bz <= hi[2]; ++bz)
+        for (int by = lo[1]; ok && by <= hi[1]; ++by)
+          for (int bx = lo[0]; ok && bx <= hi[0]; ++bx) {
+            if (d.refined[d.at(bx, by, bz)]) ok = false;
+            for (int dz = -1; dz <= 1; ++dz)
+              for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx)
+                  if (!d.reg(bx + dx, by + dy, bz + dz)) ok = false;
+          }
+      if (ok) {
+        ln = l;
+        for (int a = 0; a < 3; ++a) box[a][0] = b[a][0], box[a][1] = b[a][1];
+      }
+    }
+    if (ln < 0)
+      return "the nozzle must lie inside non-refined blocks of one level, one block away from its "
+             "interfaces and the domain faces";
+    P.nozzle_level = ln;
+    LevelPlan& lp = P.lv[ln];
+    const double s = std::ldexp(1.0, -ln);
+    // cell-centre test of the closed cylinder (coarse units)
+    auto solid = [&](int X, int Y, int Z) {
+      const double xc = (X + 0.5) * s, yc = (Y + 0.5) * s, zc = (Z + 0.5) * s;
+      const double dy = yc - y0, dz = zc - z0;
+      return xc >= x0 && xc <= x1 && dy * dy + dz * dz <= R * R;
+    };
+    int clo[3], chi[3];
+    for (int a = 0; a < 3; ++a) {
+      clo[a] = int(std::floor(box[a][0]));
+      chi[a] = int(std::ceil(box[a][1]));
+    }
+    auto loc = [&](int X, int Y, int Z, int32_t& b, int16_t& c) {
+      b = lp.box_id(X >> 3, Y >> 3, Z >> 3);
+      c = int16_t((X & 7) + 8 * (Y & 7) + 64 * (Z & 7));
+      return b >= 0;
+    };
+    // solid cells leave the stream-collide work (masked items)
+    std::vector<int32_t> item_of(size_t(lp.nblocks()), -1);
+    for (size_t k = 0; k < lp.items.size(); ++k) item_of[lp.items[k].block] = int32_t(k);
+    std::vector<char> drop(lp.items.size(), 0);
+    for (int Z = clo[2]; Z <= chi[2]; ++Z)
+      for (int Y = clo[1]; Y <= chi[1]; ++Y)
+        for (int X = clo[0]; X <= chi[0]; ++X) {
+          if (!solid(X, Y, Z)) continue;
+          int32_t b;
+          int16_t c;
+          if (!loc(X, Y, Z, b, c) || lp.kind[int64_t(b) * 512 + c] != K_ACTIVE || item_of[b] < 0)
+            return "internal: nozzle cell outside the active cells of its level";
+          lp.kind[int64_t(b) * 512 + c] = K_SOLID;
+          lp.solid_cells++;
+          lp.active_cells--;
+          lp.updated_cells--;
+          WorkItem& w = lp.items[item_of[b]];
+          if (w.mask < 0) {
+            if (lp.masks.size() / 16 >= 32767) return "too many masked blocks";
+            w.mask = int16_t(lp.masks.size() / 16);
+            lp.masks.insert(lp.masks.end(), 16, 0xffffffffu);
+          }
+          uint32_t* m = &lp.masks[size_t(w.mask) * 16];
+          m[c >> 5] &= ~(1u << (c & 31));
+        }
+    for (size_t k = 0; k < lp.items.size(); ++k) {
+      const WorkItem& w = lp.items[k];
+      if (w.mask < 0) continue;
+      bool any = false;
+      for (int j = 0; j < 16; ++j) any = any || lp.masks[size_t(w.mask) * 16 + j] != 0;
+      drop[k] = !any;
+    }
+    {
+      std::vector<WorkItem> keep;
+      for (size_t k = 0; k < lp.items.size(); ++k)
+        if (!drop[k]) keep.push_back(lp.items[k]);
+      lp.items.swap(keep);
+    }
+    // links: fluid cells whose neighbour along e_i is solid; the segment
+    // between the cell centres enters the cylinder at the later of its
+    // entries into the slab x0 <= x <= x1 and the infinite cylinder r <= R
+    const int Q = P.Q;
+    for (int Z = clo[2]; Z <= chi[2]; ++Z)
+      for (int Y = clo[1]; Y <= chi[1]; ++Y)
+        for (int X = clo[0]; X <= chi[0]; ++X) {
+          if (solid(X, Y, Z)) continue;
+          for (int i = 1; i < Q; ++i) {
+            const int ex = Q == 19 ? Lattice<19>::ex(i) : Lattice<27>::ex(i);
+            const int ey = Q == 19 ? Lattice<19>::ey(i) : Lattice<27>::ey(i);
+            const int ez = Q == 19 ? Lattice<19>::ez(i) : Lattice<27>::ez(i);
+            if (!solid(X + ex, Y + ey, Z + ez)) continue;
+            LinkItem it{};
+            if (!loc(X, Y, Z, it.fblock, it.fcell) || lp.kind[int64_t(it.fblock) * 512 + it.fcell] != K_ACTIVE ||
+                !loc(X + ex, Y + ey, Z + ez, it.bblock, it.bcell))
+              return "internal: nozzle link outside the active cells of its level";
+            it.i = uint8_t(i);
+            it.ib = uint8_t(Q == 19 ? Lattice<19>::index(-ex, -ey, -ez) : Lattice<27>::index(-ex, -ey, -ez));
+            const double px = (X + 0.5) * s, py = (Y + 0.5) * s - y0, pz = (Z + 0.5) * s - z0;
+            const double dx = ex * s, dy = ey * s, dz = ez * s;
+            double ts;
+            bool cap1 = false;
+            if (px >= x0 && px <= x1) {
+              ts = 0.0;
+            } else if (px > x1) {
+              ts = (x1 - px) / dx;
+              cap1 = true;
+            } else {
+              ts = (x0 - px) / dx;
+            }
+            const double cc = py * py + pz * pz - R * R;
+            double tc = 0.0;
+            if (cc > 0) {
+              const double aa = dy * dy + dz * dz;
+              const double bb = 2.0 * (py * dy + pz * dz);
+              tc = (-bb - std::sqrt(bb * bb - 4.0 * aa * cc)) / (2.0 * aa);
+            }
+            if (ts >= tc) {
+              it.q = ts;
+            } else {
+              it.q = tc;
+              cap1 = false;
+            }
+            it.type = cap1 ? 1 : 0;
+            it.y = Y + ey;
+            it.z = Z + ez;
+            if (cap1) {
+              // the fluid cell straight downstream of the solid cell
+              if (!loc(X + ex + 1, Y + ey, Z + ez, it.sblock, it.scell) ||
+                  lp.kind[int64_t(it.sblock) * 512 + it.scell] != K_ACTIVE)
+                return "internal: cap link without a fluid cell downstream";
+            } else if (solid(X - ex, Y - ey, Z - ez)) {
+              it.sblock = -1;
+            } else if (!loc(X - ex, Y - ey, Z - ez, it.sblock, it.scell) ||
+                       lp.kind[int64_t(it.sblock) * 512 + it.scell] != K_ACTIVE) {
+              return "internal: nozzle link's second cell is not active";
+            }
+            lp.links.push_back(it);
+          }
+        }
+  }
+
   // ---------------------------------------------------------------- memory estimate
   const size_t sb = storage_bytes(storage);
   const bool aux = model == LBM_D3Q19_MRT_LES && L > 1;
@@ -565,7 +726,7 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
     bytes += int64_t(lp.items.size() * sizeof(WorkItem) + lp.masks.size() * 4 +
                      lp.c2f.size() * sizeof(C2FItem) + lp.c2f_chunks.size() * sizeof(C2FChunk) +
                      lp.c2f_cells.size() * sizeof(C2FCell) + lp.f2c.size() * sizeof(F2CItem) +
-                     (lp.bc.size() + lp.c2f_bc.size()) * sizeof(BCItem));
+                     (lp.bc.size() + lp.c2f_bc.size()) * sizeof(BCItem) + lp.links.size() * sizeof(LinkItem));
   }
   P.device_bytes = bytes;
   return "";

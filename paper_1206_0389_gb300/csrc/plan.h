@@ -34,10 +34,11 @@ struct LevelPlan {
   std::vector<BCItem> bc;           // inflow ghost cells
   std::vector<BCItem> c2f_bc;       // inflow ghosts whose source is a c2f ghost cell
                                     // (written by the coarse-to-fine kernel)
+  std::vector<LinkItem> links;      // nozzle surface links (the nozzle's level only)
   std::vector<int32_t> block_of;    // [nbz][nby][nbx] in-domain block -> box id or -1
 
   int64_t level_blocks = 0, active_cells = 0, updated_cells = 0, hidden_cells = 0;
-  int64_t ghost_cells = 0, bc_cells = 0;
+  int64_t ghost_cells = 0, bc_cells = 0, solid_cells = 0;
 
   // box id of level block (bx, by, bz) given in level coordinates, -1 if
   // outside the box
@@ -50,6 +51,7 @@ struct GridPlan {
   bool periodic_x = true;
   int walls = 0, slip = 0;  // level-0 wall faces (bit 0/1 low/high y, 2/3 low/high z), free-slip subset
   int outlet = 0;           // 1: pressure outlet on x = NX (level 0)
+  int nozzle_level = -1;    // level holding the nozzle, -1 if none
   std::vector<LevelPlan> lv;
   int64_t device_bytes = 0;
 };

@@ -39,7 +39,8 @@ class LbmError(RuntimeError):
 class lbm_grid(ctypes.Structure):
     _fields_ = [("nbx", c_int), ("nby", c_int), ("nbz", c_int), ("periodic_x", c_int),
                 ("levels", c_int), ("refine", POINTER(c_uint8)), ("walls", c_int), ("slip", c_int),
-                ("outlet", c_int)]
+                ("outlet", c_int), ("nozzle_y0", c_double), ("nozzle_z0", c_double), ("nozzle_r", c_double),
+                ("nozzle_x0", c_double), ("nozzle_x1", c_double)]
 
 
 class lbm_plan_info(ctypes.Structure):
@@ -47,7 +48,8 @@ class lbm_plan_info(ctypes.Structure):
         (n, c_int64 * LBM_MAX_LEVELS) for n in
         ("blocks", "level_blocks", "active_cells", "updated_cells", "hidden_cells", "ghost_cells",
          "bc_cells")] + [("updates_per_coarse_step", c_int64),
-                         ("active_updates_per_coarse_step", c_int64), ("device_bytes", c_int64)]
+                         ("active_updates_per_coarse_step", c_int64), ("device_bytes", c_int64),
+                         ("nozzle_level", c_int), ("solid_cells", c_int64), ("nozzle_links", c_int64)]
 
 
 _lib = None
@@ -112,21 +114,24 @@ def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
 
 
-def make_grid(nb, periodic_x=True, refine=(), walls=0, slip=0, outlet=0):
+def make_grid(nb, periodic_x=True, refine=(), walls=0, slip=0, outlet=0, nozzle=None):
     """lbm_grid from coarse block counts nb = (nbx, nby, nbz), refine flags
     (list of arrays shaped (nbz*2^l, nby*2^l, nbx*2^l)), the wall faces
-    (bit 0/1 low/high y, 2/3 low/high z; slip the free-slip subset) and the
-    outlet type (0 zero-gradient, 1 fixed pressure).  Returns (grid, keepalive)."""
+    (bit 0/1 low/high y, 2/3 low/high z; slip the free-slip subset), the
+    outlet type (0 zero-gradient, 1 fixed pressure) and the nozzle
+    (y0, z0, r, x0, x1) or None.  Returns (grid, keepalive)."""
     flags = [np.ascontiguousarray(np.asarray(r, dtype=np.uint8)).reshape(-1) for r in refine]
     buf = np.concatenate(flags) if flags else np.zeros(1, dtype=np.uint8)
     g = lbm_grid(int(nb[0]), int(nb[1]), int(nb[2]), 1 if periodic_x else 0, len(flags) + 1,
-                 buf.ctypes.data_as(POINTER(c_uint8)), int(walls), int(slip), int(outlet))
+                 buf.ctypes.data_as(POINTER(c_uint8)), int(walls), int(slip), int(outlet),
+                 *(float(v) for v in (nozzle if nozzle is not None else (0, 0, 0, 0, 0))))
     return g, buf
 
 
-def lbm_plan(nb, periodic_x=True, refine=(), model="d3q19", storage="f32", walls=0, slip=0, outlet=0):
+def lbm_plan(nb, periodic_x=True, refine=(), model="d3q19", storage="f32", walls=0, slip=0, outlet=0,
+             nozzle=None):
     lib = load()
-    g, keep = make_grid(nb, periodic_x, refine, walls, slip, outlet)
+    g, keep = make_grid(nb, periodic_x, refine, walls, slip, outlet, nozzle)
     info = lbm_plan_info()
     st = lib.lbm_plan(ctypes.byref(g), MODELS[model], STORAGES[storage], ctypes.byref(info))
     if st != LBM_OK:
@@ -160,9 +165,9 @@ def _check(ctx, st):
 
 
 def lbm_create(model, storage, nb, periodic_x=True, refine=(), omega=1.0, cs=0.0, stream=None,
-               walls=0, slip=0, outlet=0):
+               walls=0, slip=0, outlet=0, nozzle=None):
     lib = load()
-    g, keep = make_grid(nb, periodic_x, refine, walls, slip, outlet)
+    g, keep = make_grid(nb, periodic_x, refine, walls, slip, outlet, nozzle)
     h = c_void_p()
     st = lib.lbm_create(ctypes.byref(h), MODELS[model], STORAGES[storage], ctypes.byref(g),
                         float(omega), float(cs), stream)

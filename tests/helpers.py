@@ -15,13 +15,13 @@ def gpu():
 
 
 def make_pair(model, storage, nb, periodic_x=True, refine=(), omega=1.6, cs=0.0, walls=0, slip=0,
-              outlet=0):
+              outlet=0, nozzle=None):
     lbm = gpu()
     ctx = lbm.lbm_create(model, storage, nb, periodic_x, [np.asarray(r) for r in refine], omega, cs,
-                         walls=walls, slip=slip, outlet=outlet)
+                         walls=walls, slip=slip, outlet=outlet, nozzle=nozzle)
     orc = NestedSolver(model, nb, periodic_x=periodic_x,
                        refine=[torch.as_tensor(np.asarray(r)).bool() for r in refine],
-                       omega=omega, cs=cs, walls=walls, slip=slip, outlet=outlet)
+                       omega=omega, cs=cs, walls=walls, slip=slip, outlet=outlet, nozzle=nozzle)
     return ctx, orc
 
 

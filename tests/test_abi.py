@@ -161,6 +161,30 @@ def test_plan_outlet_rules_match_oracle():
             NestedSolver("d3q27", (3, 2, 2), **bad_args)
 
 
+@pytest.mark.parametrize("model", ["d3q19", "d3q27"])
+def test_plan_nozzle_matches_oracle(model):
+    """The planner and the oracle pick the same level for the nozzle and agree
+    on its solid cells, its links and the remaining active cells."""
+    cases = [((5, 5, 5), [], (20.0, 20.0, 4.3, 10.25, 24.0), 0)]
+    r = np.zeros((5, 5, 5), dtype=bool)
+    r[1:4, 1:4, 1:4] = True
+    cases.append(((5, 5, 5), [r], (20.0, 20.0, 1.3, 18.25, 21.5), 1))
+    for nb, ref, noz, level in cases:
+        info = lbm.lbm_plan(nb, False, ref, model, "f32", nozzle=noz)
+        s = NestedSolver(model, nb, periodic_x=False, refine=[torch.from_numpy(x) for x in ref], nozzle=noz)
+        assert info.nozzle_level == s.body.l == level
+        assert info.solid_cells == int(s.body.solid.sum())
+        assert info.nozzle_links == len(s.body.q)
+        for l, lv in enumerate(s.levels):
+            assert info.active_cells[l] == int(lv.active.sum())
+            assert info.updated_cells[l] == int(lv.update.sum())
+    with pytest.raises(lbm.LbmError):                 # next to the level-1 interface
+        lbm.lbm_plan((5, 5, 5), False, [r], model, "f32", nozzle=(20.0, 20.0, 4.3, 10.25, 24.0))
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_plan((5, 5, 5), False, [], model, "f32", nozzle=(20.0, 20.0, 4.3, 24.0, 10.0))
+    assert lbm.lbm_plan((5, 5, 5), False, [], model, "f32").nozzle_level == -1
+
+
 def test_create_without_gpu_reports_cuda_error():
     if torch.cuda.is_available():
         pytest.skip("a GPU is present")
