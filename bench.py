@@ -218,16 +218,26 @@ def velocity_error(lbm, ctx, ref_u):
     return float(np.sqrt(((u - ref_u) ** 2).sum() / (ref_u ** 2).sum()))
 
 
-def run_jet(lbm, torch, model, steps, warmup, stream, walls=0, slip=0):
+def run_jet(lbm, torch, model, steps, warmup, stream, walls=0, slip=0, paper_tank=False):
     """2-level jet (coarse 384x192x192, fine cylinder of radius 24 coarse
-    cells); walls/slip put it in a tank (y/z wall faces, free-slip subset)."""
+    cells); walls/slip put it in a tank (y/z wall faces, free-slip subset).
+    paper_tank adds the rest of the paper's setup: the pressure outlet (the
+    refinement then stops one block before it) and the nozzle, a cylinder
+    of diameter 16 from x = 8 to 48 (coarse cells) on the fine level whose
+    cap emits the jet."""
     import synth
     flags, centre = synth.jet_two_level()
+    outlet, nozzle = 0, None
+    if paper_tank:
+        flags = [flags[0].copy()]
+        flags[0][:, :, -1] = False
+        outlet, nozzle = 1, (centre[0], centre[1], 8.0, 8.0, 48.0)
+    kw = dict(walls=walls, slip=slip, outlet=outlet, nozzle=nozzle)
     nu_c = 0.05 * 16 / 1e4
     ctx = lbm.lbm_create(model, "f32", (48, 24, 24), False, flags, 1.0 / (3 * nu_c + 0.5),
-                         0.18 if model == "d3q19" else 0.0, stream.cuda_stream, walls=walls, slip=slip)
+                         0.18 if model == "d3q19" else 0.0, stream.cuda_stream, **kw)
     lbm.lbm_set_inflow(ctx, centre[0], centre[1], 16.0, 0.05, 0.01, 389)
-    info = lbm.lbm_plan((48, 24, 24), False, flags, model, "f32", walls=walls, slip=slip)
+    info = lbm.lbm_plan((48, 24, 24), False, flags, model, "f32", **kw)
     lbm.lbm_step(ctx, warmup)
     lbm.lbm_sync(ctx)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -387,18 +397,27 @@ def ours(args):
     field = synth.spectrum_field(N_GRID, seed=1206 + rank)
     K, W = args.steps, args.warmup
 
-    if args.kernel_only and args.variant.startswith(("jet2s_", "jet2t_", "jet3s_", "jet3p_")):
+    if args.kernel_only and args.variant.startswith(("jet2s_", "jet2t_", "jet2p_", "jet3s_", "jet3p_")):
         # jets for profiling the interface and boundary kernels:
         # jet2s = 2 levels (coarse 192x96x96, fine cylinder of radius 12);
         # jet2t = jet2s in a tank (no-slip sides and bottom, free-slip top);
+        # jet2p = the paper's tank at that size: walls, pressure outlet and the
+        # nozzle (diameter 8, x = 8..24) on the fine level (refinement radius 20);
         # jet3s = the 3-level jet at half the paper's scale (coarse
         # 256x128x128, D = 16, 1.8 GB in FP32); jet3p = the paper-scale
         # 3-level jet (11.3 GB in FP32: launch lists only, no full captures)
         kind, model, storage = args.variant.split("_")
-        walls, slip = (15, 8) if kind == "jet2t" else (0, 0)
+        walls, slip = (15, 8) if kind in ("jet2t", "jet2p") else (0, 0)
+        outlet, nozzle = 0, None
         if kind in ("jet2s", "jet2t"):
             nb, D = (24, 12, 12), 8.0
             flags, centre = synth.jet_two_level(*nb, radius=12.0)
+        elif kind == "jet2p":
+            nb, D = (24, 12, 12), 8.0
+            flags, centre = synth.jet_two_level(*nb, radius=20.0)
+            flags = [flags[0].copy()]
+            flags[0][:, :, -1] = False
+            outlet, nozzle = 1, (centre[0], centre[1], 4.0, 8.0, 24.0)
         elif kind == "jet3p":
             nb, D = (64, 32, 32), 32.0
             flags, centre = synth.jet_paper_scale()
@@ -406,7 +425,8 @@ def ours(args):
             nb, D = (32, 16, 16), 16.0
             flags, centre = synth.jet_three_level(*nb, r1=(4.0, 16.0), r2=(6.0, 12.0), x1=(0, 96), x2=(0, 48))
         ctx = lbm.lbm_create(model, storage, nb, False, flags, 1.0 / (3 * 8e-5 + 0.5),
-                             0.18 if model == "d3q19" else 0.0, stream.cuda_stream, walls=walls, slip=slip)
+                             0.18 if model == "d3q19" else 0.0, stream.cuda_stream, walls=walls, slip=slip,
+                             outlet=outlet, nozzle=nozzle)
         lbm.lbm_set_inflow(ctx, centre[0], centre[1], D, 0.05, 0.01, 389)
         lbm.lbm_step(ctx, W)
         lbm.lbm_set_profiling(ctx, True)
@@ -510,6 +530,9 @@ def ours(args):
         # the same jet in a tank: no-slip side walls and bottom, free-slip top
         variants["jet_2level_tank_d3q27_f32"] = run_jet(lbm, torch, "d3q27", max(10, K // 4), 3, stream,
                                                         walls=15, slip=8)
+        # and the paper's whole tank: plus the pressure outlet and the nozzle
+        variants["jet_2level_paper_tank_d3q27_f32"] = run_jet(lbm, torch, "d3q27", max(10, K // 4), 3, stream,
+                                                              walls=15, slip=8, paper_tank=True)
         for storage in ("f32", "f16"):
             variants["jet_3level_d3q27_%s" % storage] = run_jet3(lbm, torch, storage, max(20, K // 4), 3, stream)
         variants["adjoint_d3q27_f32"] = run_adjoint(lbm, torch, stream)
@@ -581,7 +604,7 @@ def main():
     ap.add_argument("--kernel-only", action="store_true",
                     help="only the stream-collide steps of one variant (for ncu captures)")
     ap.add_argument("--variant", default="d3q27_f32",
-                    help="for --kernel-only: model_storage (e.g. d3q19_f16), jet2s_/jet2t_/jet3s_/jet3p_"
+                    help="for --kernel-only: model_storage (e.g. d3q19_f16), jet2s_/jet2t_/jet2p_/jet3s_/jet3p_"
                          "model_storage, or adjoint")
     args = ap.parse_args()
     if args.warmup < 3:
