@@ -252,3 +252,15 @@ def test_cap_inflow_with_the_wrong_density_cell_is_caught(monkeypatch):
             b.b_idx = keep
     monkeypatch.setattr(S.NestedSolver, "_body_links", links)
     assert fails(TZ.test_cap_inflow_equals_face_inflow, "d3q27")
+
+
+def test_half_width_at_half_maximum_is_caught(monkeypatch):
+    """A spreading width taken where u falls to u_m / 2 instead of u_m / e."""
+    import types
+    import oracle.jetstats as J
+    from tests import test_oracle_jetstats as TJ
+    fake = types.SimpleNamespace(**{k: getattr(math, k) for k in dir(math) if not k.startswith("_")})
+    fake.e = 2.0
+    monkeypatch.setattr(J, "math", fake)
+    assert fails(TJ.test_gaussian_profile_gives_its_width_and_unit_fit)
+    assert fails(TJ.test_parabolic_profile_half_width_closed_form)
