@@ -202,6 +202,31 @@ int lbm_stats_reset(lbm_ctx* ctx);
 int lbm_stats_accumulate(lbm_ctx* ctx);
 int lbm_stats_get(lbm_ctx* ctx, int level, double* mean, double* var, int64_t* nsamples);
 
+/* The jet's radial profiles on cross-sections (Section 3.3 evaluates the
+ * mean axial velocity, the spreading width, the radial Gaussian profile and
+ * the turbulence intensity), computed on the device from the accumulated
+ * statistics of one level.  For station s (x[s] in coarse-cell units: the
+ * layer of level cells containing it) and ring b (cell centres at distance
+ * r in [b dr, (b + 1) dr) from the axis (y0, z0), coarse units), over the
+ * cells of the layer that hold a value of the level: counts[s][b],
+ * mean_ux[s][b] the average of the time mean of u_x and var_ux[s][b] the
+ * average of its time variance (NaN for empty rings).  Arrays are
+ * [nstations][nbins].  LBM_ERR_STATE before any sample; LBM_ERR_ARG for a
+ * station outside the level or dr <= 0. */
+int lbm_stats_radial(lbm_ctx* ctx, int level, double y0, double z0, double dr, int nbins, int nstations,
+                     const double* x, double* mean_ux, double* var_ux, int64_t* counts);
+
+/* Jet quantities of one station's ring profile (host arithmetic, no
+ * context): out = {u_m, b_e, tI, a, c} with u_m the value of ring 0, b_e the
+ * half width where the profile falls to u_m / e (0.368 u_m; linear between
+ * the centres (b + 1/2) dr of the first ring at or below it and the ring
+ * before), tI = sqrt(max(var_0, 0)) / u_m, and a, c the least-squares fit
+ * u / u_m = a exp(-c (r / b_e)^2) of ln(u / u_m) over the rings with cells,
+ * u >= 0.05 u_m and r <= 2 b_e (the paper quotes a = 0.938, c = 0.944).
+ * Undefined entries are NaN.  LBM_ERR_ARG for NULL or nbins < 1. */
+int lbm_jet_fit(int nbins, double dr, const double* mean_ux, const double* var_ux, const int64_t* counts,
+                double out[5]);
+
 /* Float64 sums over the unrefined cells of all levels, weighted by the cell
  * volume 8^-l: out = {sum (rho - 1), sum j_x, sum j_y, sum j_z}, j = sum f e.
  * LBM_ERR_NONFINITE if any summed value is NaN/Inf. */

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <limits>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -924,6 +925,120 @@ int lbm_stats_get(lbm_ctx* ctx, int level, double* mean, double* var, int64_t* n
   if (nsamples) *nsamples = ctx->stats_n;
   return slab_transfer(ctx, level, SLAB_GET_STATS, nullptr, hout, 7, nullptr, ctx->dl[level].stats,
                        1.0 / double(ctx->stats_n));
+}
+
+int lbm_stats_radial(lbm_ctx* ctx, int level, double y0, double z0, double dr, int nbins, int nstations,
+                     const double* x, double* mean_ux, double* var_ux, int64_t* counts) {
+  if (!ctx || !x || !mean_ux || !var_ux || !counts) return fail(ctx, LBM_ERR_ARG, "NULL argument");
+  if (level < 0 || level >= ctx->L) return fail(ctx, LBM_ERR_ARG, "level out of range");
+  if (!std::isfinite(y0) || !std::isfinite(z0) || !std::isfinite(dr))
+    return fail(ctx, LBM_ERR_NONFINITE, "non-finite profile parameter");
+  if (!(dr > 0) || nbins < 1 || nstations < 1 || int64_t(nbins) * nstations > (int64_t(1) << 24))
+    return fail(ctx, LBM_ERR_ARG, "need dr > 0, nbins >= 1, nstations >= 1");
+  if (!ctx->dl[0].stats || ctx->stats_n == 0) return fail(ctx, LBM_ERR_STATE, "no samples accumulated");
+  const LevelPlan& lp = ctx->plan.lv[level];
+  std::vector<int> xs(static_cast<size_t>(nstations));
+  for (int s = 0; s < nstations; ++s) {
+    if (!std::isfinite(x[s])) return fail(ctx, LBM_ERR_NONFINITE, "non-finite station");
+    const double X = std::floor(std::ldexp(x[s], level));
+    if (X < 0 || X >= lp.NX) return fail(ctx, LBM_ERR_ARG, "station outside the level");
+    xs[size_t(s)] = int(X);
+  }
+  const size_t nb = size_t(nbins) * nstations;
+  double* acc = nullptr;
+  unsigned long long* cnt = nullptr;
+  int* dxs = nullptr;
+  cudaError_t e = cudaMalloc(&acc, nb * 2 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&cnt, nb * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&dxs, xs.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, nb * 2 * sizeof(double), ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, nb * sizeof(unsigned long long), ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dxs, xs.data(), xs.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+  std::vector<double> hacc(nb * 2);
+  std::vector<unsigned long long> hcnt(nb);
+  if (e == cudaSuccess) {
+    RadialArgs a{};
+    a.sums = ctx->dl[level].stats;
+    a.kind = ctx->dl[level].kind;
+    a.ox = lp.ox;
+    a.oy = lp.oy;
+    a.oz = lp.oz;
+    a.BX = lp.BX;
+    a.BY = lp.BY;
+    a.BZ = lp.BZ;
+    a.NY = lp.NY;
+    a.NZ = lp.NZ;
+    a.xs = dxs;
+    a.nst = nstations;
+    a.nbins = nbins;
+    a.y0 = y0;
+    a.z0 = z0;
+    a.dr = dr;
+    a.inv_scale = std::ldexp(1.0, -level);
+    a.scale = 1.0 / double(ctx->stats_n);
+    a.acc = acc;
+    a.cnt = cnt;
+    e = launch_radial(a, ctx->stream);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hacc.data(), acc, nb * 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hcnt.data(), cnt, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(acc);
+  cudaFree(cnt);
+  cudaFree(dxs);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "radial profile");
+  const double nan = std::numeric_limits<double>::quiet_NaN();
+  for (size_t o = 0; o < nb; ++o) {
+    counts[o] = int64_t(hcnt[o]);
+    mean_ux[o] = hcnt[o] ? hacc[2 * o] / double(hcnt[o]) : nan;
+    var_ux[o] = hcnt[o] ? hacc[2 * o + 1] / double(hcnt[o]) : nan;
+  }
+  return LBM_OK;
+}
+
+int lbm_jet_fit(int nbins, double dr, const double* mean_ux, const double* var_ux, const int64_t* counts,
+                double out[5]) {
+  if (!mean_ux || !var_ux || !counts || !out || nbins < 1 || !(dr > 0)) return LBM_ERR_ARG;
+  const double nan = std::numeric_limits<double>::quiet_NaN();
+  for (int k = 0; k < 5; ++k) out[k] = nan;
+  if (counts[0] == 0 || !(mean_ux[0] > 0)) return LBM_OK;
+  const double um = mean_ux[0];
+  out[0] = um;
+  out[2] = std::sqrt(std::max(var_ux[0], 0.0)) / um;
+  // half width: first ring at or below u_m / e, linear between ring centres
+  const double lev = um / std::exp(1.0);
+  double be = nan;
+  for (int b = 1; b < nbins; ++b) {
+    if (counts[b] == 0 || counts[b - 1] == 0) continue;
+    if (mean_ux[b] <= lev) {
+      be = (b - 0.5) * dr + (mean_ux[b - 1] - lev) / (mean_ux[b - 1] - mean_ux[b]) * dr;
+      break;
+    }
+  }
+  if (!std::isfinite(be)) return LBM_OK;
+  out[1] = be;
+  // least squares of ln(u / u_m) against (r / b_e)^2
+  double n = 0, sx = 0, sy = 0, sxx = 0, sxy = 0;
+  for (int b = 0; b < nbins; ++b) {
+    const double r = (b + 0.5) * dr;
+    if (counts[b] > 0 && mean_ux[b] >= 0.05 * um && r <= 2.0 * be) {
+      const double X = (r / be) * (r / be), Y = std::log(mean_ux[b] / um);
+      n += 1;
+      sx += X;
+      sy += Y;
+      sxx += X * X;
+      sxy += X * Y;
+    }
+  }
+  const double den = n * sxx - sx * sx;
+  if (n < 2 || den == 0) return LBM_OK;
+  const double slope = (n * sxy - sx * sy) / den;
+  out[3] = std::exp((sy - slope * sx) / n);
+  out[4] = -slope;
+  return LBM_OK;
 }
 
 int lbm_mass_momentum(lbm_ctx* ctx, double out[4]) {

@@ -242,6 +242,22 @@ struct StatsArgs {
   double* sums;
 };
 cudaError_t launch_stats(int model, int storage, const StatsArgs& a, cudaStream_t st);
+
+// ring sums of the time mean and variance of u_x on cross-sections x = const
+// of one level: thread per (station, y, z) cell; float64 atomics into
+// acc[station][ring][2] and cnt[station][ring]
+struct RadialArgs {
+  const double* sums;     // statistics sums [7][nblocks*512]
+  const uint8_t* kind;
+  int ox, oy, oz, BX, BY, BZ;
+  int NY, NZ;
+  const int* xs;          // level cell x of each station
+  int nst, nbins;
+  double y0, z0, dr, inv_scale, scale;  // scale = 1 / samples
+  double* acc;
+  unsigned long long* cnt;
+};
+cudaError_t launch_radial(const RadialArgs& a, cudaStream_t st);
 cudaError_t launch_slab(int model, int storage, const SlabArgs& a, cudaStream_t st);
 cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t st);
 // float copy of a float64 array (the compute-type body force of FP32/FP16 storage)

@@ -264,6 +264,36 @@ __global__ void k_stats(const StatsArgs a) {
   for (int c = 0; c < 7; ++c) a.sums[c * a.ncells + j] += v[c];
 }
 
+__global__ void k_radial(const RadialArgs a) {
+  const int64_t per = int64_t(a.NY) * a.NZ;
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= per * a.nst) return;
+  const int s = int(t / per);
+  const int y = int(t % a.NY), z = int((t % per) / a.NY);
+  const int64_t j = box_index(a.xs[s], y, z, a.ox, a.oy, a.oz, a.BX, a.BY, a.BZ);
+  if (j < 0) return;
+  const uint8_t k = a.kind[j];
+  if (k != K_ACTIVE && k != K_HIDDEN1 && k != K_HIDDEN2) return;
+  const double dy = (y + 0.5) * a.inv_scale - a.y0, dz = (z + 0.5) * a.inv_scale - a.z0;
+  const double r = sqrt(__dadd_rn(__dmul_rn(dy, dy), __dmul_rn(dz, dz)));
+  const int b = int(floor(r / a.dr));
+  if (b >= a.nbins) return;
+  const int64_t nn = int64_t(a.BX) * a.BY * a.BZ * kCells;
+  const double m = a.sums[nn + j] * a.scale;
+  const double v = a.sums[4 * nn + j] * a.scale - m * m;
+  const int64_t o = int64_t(s) * a.nbins + b;
+  atomicAdd(a.acc + 2 * o, m);
+  atomicAdd(a.acc + 2 * o + 1, v);
+  atomicAdd(a.cnt + o, 1ull);
+}
+
+cudaError_t launch_radial(const RadialArgs& a, cudaStream_t st) {
+  const int64_t n = int64_t(a.NY) * a.NZ * a.nst;
+  if (n == 0) return cudaSuccess;
+  k_radial<<<unsigned((n + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <class M, class S>
 static cudaError_t stats_ms(const StatsArgs& a, cudaStream_t st) {
   if (a.ncells == 0) return cudaSuccess;

@@ -26,7 +26,8 @@ EXPORTED = ["lbm_plan", "lbm_create", "lbm_create_error", "lbm_set_inflow", "lbm
             "lbm_set_profiling", "lbm_get_profile", "lbm_get_tuning", "lbm_last_error", "lbm_destroy",
             "lbm_mass_momentum_noalloc", "lbm_adjoint_forward", "lbm_adjoint_backward",
             "lbm_get_strain", "lbm_set_strain", "lbm_raw_state_bytes", "lbm_get_raw_state",
-            "lbm_set_raw_state", "lbm_stats_reset", "lbm_stats_accumulate", "lbm_stats_get"]
+            "lbm_set_raw_state", "lbm_stats_reset", "lbm_stats_accumulate", "lbm_stats_get",
+            "lbm_stats_radial", "lbm_jet_fit"]
 NOALLOC_MAX_BLOCKS = 65536
 
 
@@ -84,6 +85,9 @@ def load():
         "lbm_stats_reset": (c_int, [c_void_p]),
         "lbm_stats_accumulate": (c_int, [c_void_p]),
         "lbm_stats_get": (c_int, [c_void_p, c_int, D, D, P(c_int64)]),
+        "lbm_stats_radial": (c_int, [c_void_p, c_int, c_double, c_double, c_double, c_int, c_int, D, D, D,
+                                     P(c_int64)]),
+        "lbm_jet_fit": (c_int, [c_int, c_double, D, D, P(c_int64), D]),
         "lbm_get_raw_state": (c_int, [c_void_p, c_int, c_void_p, c_size_t]),
         "lbm_set_raw_state": (c_int, [c_void_p, c_int, c_void_p, c_size_t]),
         "lbm_set_strain": (c_int, [c_void_p, c_int, D, c_size_t]),
@@ -251,6 +255,28 @@ def lbm_stats_get(ctx, level):
     n = c_int64()
     _check(ctx, load().lbm_stats_get(ctx.h, level, _dptr(mean), _dptr(var), ctypes.byref(n)))
     return mean, var, n.value
+
+
+def lbm_stats_radial(ctx, level, y0, z0, dr, nbins, x_stations):
+    """Ring profiles (mean_ux, var_ux, counts), each [nstations][nbins]."""
+    xs = _f64(np.asarray(x_stations, dtype=np.float64).reshape(-1))
+    m = np.empty((len(xs), int(nbins)))
+    v = np.empty_like(m)
+    c = np.empty(m.shape, dtype=np.int64)
+    _check(ctx, load().lbm_stats_radial(ctx.h, int(level), float(y0), float(z0), float(dr), int(nbins), len(xs),
+                                        _dptr(xs), _dptr(m), _dptr(v), c.ctypes.data_as(POINTER(c_int64))))
+    return m, v, c
+
+
+def lbm_jet_fit(mean_ux, var_ux, counts, dr):
+    """(u_m, b_e, tI, a, c) of one station's ring profile."""
+    m, v = _f64(mean_ux), _f64(var_ux)
+    c = np.ascontiguousarray(counts, dtype=np.int64)
+    out = np.empty(5)
+    st = load().lbm_jet_fit(len(m), float(dr), _dptr(m), _dptr(v), c.ctypes.data_as(POINTER(c_int64)), _dptr(out))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_jet_fit")
+    return tuple(float(x) for x in out)
 
 
 def lbm_raw_state_bytes(ctx, level):

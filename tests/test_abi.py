@@ -194,3 +194,28 @@ def test_create_without_gpu_reports_cuda_error():
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_create("d3q19", "f32", (2, 2, 2), omega=2.5)
     assert e.value.status == lbm.LBM_ERR_ARG
+
+
+def test_jet_fit_matches_oracle_on_the_host():
+    """lbm_jet_fit (host arithmetic in the library) against the oracle's
+    statement on noisy Gaussian, parabolic, uniform and empty profiles."""
+    import math
+    from oracle.jetstats import jet_fit, radial_profile
+    N, Y0 = 96, 48.3
+    y = np.arange(N) + 0.5
+    r = np.sqrt((y[None, :] - Y0) ** 2 + (y[:, None] - Y0) ** 2)
+    rng = np.random.default_rng(5)
+    fields = [0.05 * np.exp(-(r / 9.0) ** 2) * (1 + 0.01 * rng.standard_normal(r.shape)),
+              np.where(r < 30, 0.04 * (1 - (r / 30) ** 2), 0.0),
+              np.full_like(r, 0.03)]
+    for fm in fields:
+        mean = np.repeat(fm[:, :, None], 2, axis=2)
+        var = np.repeat((1e-5 * np.abs(fm))[:, :, None], 2, axis=2)
+        for dr in (1.0, 1.7):
+            pm, pv, pc = radial_profile(mean, var, 0, Y0, Y0, dr, 40, [0.5])
+            o = jet_fit(pm[0], pv[0], pc[0], dr)
+            g = lbm.lbm_jet_fit(pm[0], pv[0], pc[0], dr)
+            for a, b in zip(o, g):
+                assert (math.isnan(a) and math.isnan(b)) or abs(a - b) <= 1e-12 * max(1.0, abs(a))
+    empty = lbm.lbm_jet_fit(np.full(5, np.nan), np.full(5, np.nan), np.zeros(5, dtype=np.int64), 1.0)
+    assert all(math.isnan(v) for v in empty)
