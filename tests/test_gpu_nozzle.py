@@ -138,3 +138,22 @@ def test_nozzle_keeps_rest_and_rejects_bad_placement():
     lbm.lbm_destroy(ctx)
     with pytest.raises(lbm.LbmError):
         lbm.lbm_create("d3q27", "f32", (5, 5, 5), False, [], 1.3, 0.0, nozzle=(20.0, 20.0, 4.3, 2.25, 24.0))
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_paper_tank_all_boundaries_f64(model):
+    """The paper's tank on a small nested grid: no-slip side walls and
+    bottom, free-slip top, pressure outlet, the nozzle on the fine level with
+    the inflow on its cap; two coarse steps against the oracle."""
+    lbm = gpu()
+    nb, ref = nested_grid()
+    ctx, orc = pair(model, "f64", nb, ref, nozzle=NOZ1, walls=15, slip=8, outlet=1)
+    lbm.lbm_set_outlet(ctx, 0.998)
+    orc.set_outlet(0.998)
+    fields = [synth.taylor_green_3d(lv.NY, 0.02, shape=(lv.NX, lv.NY, lv.NZ)) for lv in orc.levels]
+    init_both(ctx, orc, fields)
+    lbm.lbm_step(ctx, 2)
+    orc.step(2)
+    d, _ = compare_levels(ctx, orc)
+    assert d <= 1e-12, d
+    lbm.lbm_destroy(ctx)
