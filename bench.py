@@ -300,6 +300,16 @@ def run_jet3(lbm, torch, storage, steps, warmup, stream):
     centreline = {"%g" % xd: round(float(axis_ux[int(xd * 32)]) / 0.05, 5) for xd in (0, 0.25, 0.5, 1, 2)}
     intensity = {"%g" % xd: round(float(np.sqrt(max(axis_var[int(xd * 32)], 0.0))) / 0.05, 5)
                  for xd in (0, 0.25, 0.5)}
+    # ring profiles over all levels (area-weighted) on cross-sections near
+    # the nozzle and the jet quantities of Section 3.3 from them
+    stations = (0.1, 0.25)
+    pm, pv, pc = lbm.lbm_stats_radial(ctx, -1, centre[0], centre[1], 1.0, 40, [xd * 32 for xd in stations])
+    profile = {}
+    for s, xd in enumerate(stations):
+        um, be, ti, a, c = lbm.lbm_jet_fit(pm[s], pv[s], pc[s], 1.0)
+        fin = lambda v, nd: round(v, nd) if np.isfinite(v) else None      # JSON has no NaN
+        profile["%g" % xd] = {"u_m_over_u_in": fin(um / 0.05, 5), "half_width_over_D": fin(be / 32, 5),
+                              "turbulence_intensity": fin(ti, 5), "gauss_a": fin(a, 4), "gauss_c": fin(c, 4)}
     total_steps = warmup + steps + 2 + 50
     lbm.lbm_destroy(ctx)
     upd = info.active_updates_per_coarse_step
@@ -314,6 +324,7 @@ def run_jet3(lbm, torch, storage, steps, warmup, stream):
             "launches_per_coarse_step": int(pn.sum()) // 2, "final_momentum_x": float(m[1]),
             "centreline_mean_ux_over_u_in_by_x_over_D": centreline,
             "centreline_rms_ux_over_u_in_by_x_over_D": intensity,
+            "jet_profile_by_x_over_D": profile,
             "statistics_window": "coarse steps %d-%d after start from rest (%d samples)" % (
                 total_steps - 50 + 1, total_steps, nsamp)}
 

@@ -210,7 +210,10 @@ int lbm_stats_get(lbm_ctx* ctx, int level, double* mean, double* var, int64_t* n
  * r in [b dr, (b + 1) dr) from the axis (y0, z0), coarse units), over the
  * cells of the layer that hold a value of the level: counts[s][b],
  * mean_ux[s][b] the average of the time mean of u_x and var_ux[s][b] the
- * average of its time variance (NaN for empty rings).  Arrays are
+ * average of its time variance (NaN for empty rings).  level = -1 takes
+ * every level of a nested grid: the unrefined cells of each level l in its
+ * layer containing x, weighted by their cross-section area 4^-l (they tile
+ * the plane), the values being area-weighted ring averages.  Arrays are
  * [nstations][nbins].  LBM_ERR_STATE before any sample; LBM_ERR_ARG for a
  * station outside the level or dr <= 0. */
 int lbm_stats_radial(lbm_ctx* ctx, int level, double y0, double z0, double dr, int nbins, int nstations,

@@ -13,6 +13,10 @@ Reading (the paper gives the quantities, not how they are sampled):
   (coarse units) whose centre lies at r in [b dr, (b + 1) dr) from the axis
   (y0, z0); its values are plain averages over those cells of the time mean
   of u_x and of the time variance of u_x;
+* over all levels of a nested grid, the unrefined (active) cells of every
+  level in its layer containing x enter, each weighted by its cross-section
+  area 4^-l (the active cells of all levels tile the plane x = const), and
+  a ring's values are area-weighted averages;
 * u_m is the value of ring 0; the half width b_e interpolates linearly
   between the centres (b + 1/2) dr of the first ring (b >= 1) at or below
   u_m / e and the ring before it;
@@ -26,37 +30,55 @@ import math
 import numpy as np
 
 
+def _rings(parts, y0, z0, dr, nbins, x_stations):
+    """Weighted ring sums over parts = [(level, mean, var, use, weight)]:
+    mean, var (NZ, NY, NX) of that level, use a boolean mask of the cells
+    that enter."""
+    ns = len(x_stations)
+    sm = np.zeros((ns, nbins))
+    sv = np.zeros((ns, nbins))
+    sw = np.zeros((ns, nbins))
+    cnt = np.zeros((ns, nbins), dtype=np.int64)
+    for level, mean_ux, var_ux, use, w in parts:
+        s = 2.0 ** -level
+        NZ, NY, NX = mean_ux.shape
+        for si, xs in enumerate(x_stations):
+            X = int(math.floor(xs * 2 ** level))
+            if not 0 <= X < NX:
+                raise ValueError("station outside the level")
+            for z in range(NZ):
+                for y in range(NY):
+                    if not use[z, y, X]:
+                        continue
+                    dy = (y + 0.5) * s - y0
+                    dz = (z + 0.5) * s - z0
+                    b = int(math.floor(math.sqrt(dy * dy + dz * dz) / dr))
+                    if b >= nbins:
+                        continue
+                    sm[si, b] += w * mean_ux[z, y, X]
+                    sv[si, b] += w * var_ux[z, y, X]
+                    sw[si, b] += w
+                    cnt[si, b] += 1
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(cnt > 0, sm / sw, np.nan), np.where(cnt > 0, sv / sw, np.nan), cnt
+
+
 def radial_profile(mean_ux, var_ux, level, y0, z0, dr, nbins, x_stations):
-    """Ring averages of the time mean and variance of u_x.
+    """Ring averages of the time mean and variance of u_x on one level.
 
     mean_ux, var_ux: (NZ, NY, NX) of level `level`, NaN where the level holds
     no value.  Returns (mean[s][b], var[s][b], counts[s][b]); NaN for empty
     rings."""
-    s = 2.0 ** -level
-    NZ, NY, NX = mean_ux.shape
-    ns = len(x_stations)
-    sm = np.zeros((ns, nbins))
-    sv = np.zeros((ns, nbins))
-    cnt = np.zeros((ns, nbins), dtype=np.int64)
-    for si, xs in enumerate(x_stations):
-        X = int(math.floor(xs * 2 ** level))
-        if not 0 <= X < NX:
-            raise ValueError("station outside the level")
-        for z in range(NZ):
-            for y in range(NY):
-                m = mean_ux[z, y, X]
-                if math.isnan(m):
-                    continue
-                dy = (y + 0.5) * s - y0
-                dz = (z + 0.5) * s - z0
-                b = int(math.floor(math.sqrt(dy * dy + dz * dz) / dr))
-                if b >= nbins:
-                    continue
-                sm[si, b] += m
-                sv[si, b] += var_ux[z, y, X]
-                cnt[si, b] += 1
-    with np.errstate(invalid="ignore", divide="ignore"):
-        return np.where(cnt > 0, sm / cnt, np.nan), np.where(cnt > 0, sv / cnt, np.nan), cnt
+    return _rings([(level, mean_ux, var_ux, ~np.isnan(mean_ux), 1.0)], y0, z0, dr, nbins, x_stations)
+
+
+def radial_profile_levels(levels, y0, z0, dr, nbins, x_stations):
+    """Area-weighted ring averages over every level of a nested grid.
+
+    levels: [(mean_ux, var_ux, active)] per level l = 0, 1, ..., with active
+    the (NZ, NY, NX) mask of the level's unrefined cells."""
+    parts = [(l, m, v, a, 4.0 ** -l) for l, (m, v, a) in enumerate(levels)]
+    return _rings(parts, y0, z0, dr, nbins, x_stations)
 
 
 def jet_fit(mean, var, counts, dr):

@@ -930,37 +930,38 @@ int lbm_stats_get(lbm_ctx* ctx, int level, double* mean, double* var, int64_t* n
 int lbm_stats_radial(lbm_ctx* ctx, int level, double y0, double z0, double dr, int nbins, int nstations,
                      const double* x, double* mean_ux, double* var_ux, int64_t* counts) {
   if (!ctx || !x || !mean_ux || !var_ux || !counts) return fail(ctx, LBM_ERR_ARG, "NULL argument");
-  if (level < 0 || level >= ctx->L) return fail(ctx, LBM_ERR_ARG, "level out of range");
+  if (level < -1 || level >= ctx->L) return fail(ctx, LBM_ERR_ARG, "level out of range");
   if (!std::isfinite(y0) || !std::isfinite(z0) || !std::isfinite(dr))
     return fail(ctx, LBM_ERR_NONFINITE, "non-finite profile parameter");
   if (!(dr > 0) || nbins < 1 || nstations < 1 || int64_t(nbins) * nstations > (int64_t(1) << 24))
     return fail(ctx, LBM_ERR_ARG, "need dr > 0, nbins >= 1, nstations >= 1");
   if (!ctx->dl[0].stats || ctx->stats_n == 0) return fail(ctx, LBM_ERR_STATE, "no samples accumulated");
-  const LevelPlan& lp = ctx->plan.lv[level];
-  std::vector<int> xs(static_cast<size_t>(nstations));
-  for (int s = 0; s < nstations; ++s) {
-    if (!std::isfinite(x[s])) return fail(ctx, LBM_ERR_NONFINITE, "non-finite station");
-    const double X = std::floor(std::ldexp(x[s], level));
-    if (X < 0 || X >= lp.NX) return fail(ctx, LBM_ERR_ARG, "station outside the level");
-    xs[size_t(s)] = int(X);
-  }
+  // one level, or every level's unrefined cells weighted by their area
+  const int l0 = level < 0 ? 0 : level, l1 = level < 0 ? ctx->L - 1 : level;
+  std::vector<int> xs(static_cast<size_t>(nstations) * (l1 - l0 + 1));
+  for (int l = l0; l <= l1; ++l)
+    for (int s = 0; s < nstations; ++s) {
+      if (!std::isfinite(x[s])) return fail(ctx, LBM_ERR_NONFINITE, "non-finite station");
+      const double X = std::floor(std::ldexp(x[s], l));
+      if (X < 0 || X >= ctx->plan.lv[l].NX) return fail(ctx, LBM_ERR_ARG, "station outside the level");
+      xs[size_t(l - l0) * nstations + s] = int(X);
+    }
   const size_t nb = size_t(nbins) * nstations;
   double* acc = nullptr;
   unsigned long long* cnt = nullptr;
   int* dxs = nullptr;
-  cudaError_t e = cudaMalloc(&acc, nb * 2 * sizeof(double));
+  cudaError_t e = cudaMalloc(&acc, nb * 3 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&cnt, nb * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&dxs, xs.size() * sizeof(int));
-  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, nb * 2 * sizeof(double), ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, nb * 3 * sizeof(double), ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, nb * sizeof(unsigned long long), ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dxs, xs.data(), xs.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
-  std::vector<double> hacc(nb * 2);
-  std::vector<unsigned long long> hcnt(nb);
-  if (e == cudaSuccess) {
+  for (int l = l0; l <= l1 && e == cudaSuccess; ++l) {
+    const LevelPlan& lp = ctx->plan.lv[l];
     RadialArgs a{};
-    a.sums = ctx->dl[level].stats;
-    a.kind = ctx->dl[level].kind;
+    a.sums = ctx->dl[l].stats;
+    a.kind = ctx->dl[l].kind;
     a.ox = lp.ox;
     a.oy = lp.oy;
     a.oz = lp.oz;
@@ -969,20 +970,24 @@ int lbm_stats_radial(lbm_ctx* ctx, int level, double y0, double z0, double dr, i
     a.BZ = lp.BZ;
     a.NY = lp.NY;
     a.NZ = lp.NZ;
-    a.xs = dxs;
+    a.xs = dxs + size_t(l - l0) * nstations;
     a.nst = nstations;
     a.nbins = nbins;
     a.y0 = y0;
     a.z0 = z0;
     a.dr = dr;
-    a.inv_scale = std::ldexp(1.0, -level);
+    a.inv_scale = std::ldexp(1.0, -l);
     a.scale = 1.0 / double(ctx->stats_n);
+    a.weight = level < 0 ? std::ldexp(1.0, -2 * l) : 1.0;
+    a.active_only = level < 0 ? 1 : 0;
     a.acc = acc;
     a.cnt = cnt;
     e = launch_radial(a, ctx->stream);
   }
+  std::vector<double> hacc(nb * 3);
+  std::vector<unsigned long long> hcnt(nb);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(hacc.data(), acc, nb * 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    e = cudaMemcpyAsync(hacc.data(), acc, nb * 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(hcnt.data(), cnt, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -993,8 +998,8 @@ int lbm_stats_radial(lbm_ctx* ctx, int level, double y0, double z0, double dr, i
   const double nan = std::numeric_limits<double>::quiet_NaN();
   for (size_t o = 0; o < nb; ++o) {
     counts[o] = int64_t(hcnt[o]);
-    mean_ux[o] = hcnt[o] ? hacc[2 * o] / double(hcnt[o]) : nan;
-    var_ux[o] = hcnt[o] ? hacc[2 * o + 1] / double(hcnt[o]) : nan;
+    mean_ux[o] = hcnt[o] ? hacc[3 * o] / hacc[3 * o + 2] : nan;
+    var_ux[o] = hcnt[o] ? hacc[3 * o + 1] / hacc[3 * o + 2] : nan;
   }
   return LBM_OK;
 }

@@ -244,8 +244,9 @@ struct StatsArgs {
 cudaError_t launch_stats(int model, int storage, const StatsArgs& a, cudaStream_t st);
 
 // ring sums of the time mean and variance of u_x on cross-sections x = const
-// of one level: thread per (station, y, z) cell; float64 atomics into
-// acc[station][ring][2] and cnt[station][ring]
+// of one level: thread per (station, y, z) cell; float64 atomics of the
+// weighted mean, weighted variance and weight into acc[station][ring][3] and
+// the cell count into cnt[station][ring]
 struct RadialArgs {
   const double* sums;     // statistics sums [7][nblocks*512]
   const uint8_t* kind;
@@ -254,6 +255,8 @@ struct RadialArgs {
   const int* xs;          // level cell x of each station
   int nst, nbins;
   double y0, z0, dr, inv_scale, scale;  // scale = 1 / samples
+  double weight;          // per cell (the cross-section area 4^-level over all levels, else 1)
+  int active_only;        // 1: unrefined cells only (all levels), 0: every cell holding a value
   double* acc;
   unsigned long long* cnt;
 };

@@ -273,7 +273,7 @@ __global__ void k_radial(const RadialArgs a) {
   const int64_t j = box_index(a.xs[s], y, z, a.ox, a.oy, a.oz, a.BX, a.BY, a.BZ);
   if (j < 0) return;
   const uint8_t k = a.kind[j];
-  if (k != K_ACTIVE && k != K_HIDDEN1 && k != K_HIDDEN2) return;
+  if (k != K_ACTIVE && (a.active_only || (k != K_HIDDEN1 && k != K_HIDDEN2))) return;
   const double dy = (y + 0.5) * a.inv_scale - a.y0, dz = (z + 0.5) * a.inv_scale - a.z0;
   const double r = sqrt(__dadd_rn(__dmul_rn(dy, dy), __dmul_rn(dz, dz)));
   const int b = int(floor(r / a.dr));
@@ -282,8 +282,9 @@ __global__ void k_radial(const RadialArgs a) {
   const double m = a.sums[nn + j] * a.scale;
   const double v = a.sums[4 * nn + j] * a.scale - m * m;
   const int64_t o = int64_t(s) * a.nbins + b;
-  atomicAdd(a.acc + 2 * o, m);
-  atomicAdd(a.acc + 2 * o + 1, v);
+  atomicAdd(a.acc + 3 * o, a.weight * m);
+  atomicAdd(a.acc + 3 * o + 1, a.weight * v);
+  atomicAdd(a.acc + 3 * o + 2, a.weight);
   atomicAdd(a.cnt + o, 1ull);
 }
 

@@ -50,6 +50,20 @@ def test_radial_profiles_match_oracle(model):
             g = lbm.lbm_jet_fit(gm[s], gv[s], gc[s], 0.9)
             for a, b in zip(o, g):
                 assert (math.isnan(a) and math.isnan(b)) or abs(a - b) <= 1e-9 * max(1.0, abs(a))
+    # every level: unrefined cells weighted by their cross-section area
+    from oracle.jetstats import radial_profile_levels
+    parts = []
+    for l in range(2):
+        mo = acc[l][0] / 3
+        vo = acc[l][1] / 3 - mo * mo
+        parts.append((mo, vo, orc.real(l, orc.levels[l].active).numpy()))
+    stations = [3.7, 9.2, 20.5]
+    pm, pv, pc = radial_profile_levels(parts, y0, z0, 0.9, 12, stations)
+    gm, gv, gc = lbm.lbm_stats_radial(ctx, -1, y0, z0, 0.9, 12, stations)
+    assert np.array_equal(gc, pc)
+    ok = pc > 0
+    assert np.abs(gm[ok] - pm[ok]).max() <= 1e-12
+    assert np.abs(gv[ok] - pv[ok]).max() <= 1e-12
     with pytest.raises(lbm.LbmError):
         lbm.lbm_stats_radial(ctx, 0, y0, z0, 0.9, 12, [40.0])      # outside the level
     lbm.lbm_destroy(ctx)

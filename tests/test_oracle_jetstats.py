@@ -60,3 +60,46 @@ def test_uniform_field_rings_counts_and_intensity():
         um, be, ti, a, c = jet_fit(pm[s], pv[s], pc[s], 1.3)
         assert abs(ti - math.sqrt(4e-6) / 0.03) <= 1e-12
         assert math.isnan(be)
+
+
+def test_levels_profile_reduces_to_one_level_and_weights_by_area():
+    """Over all levels: rings that lie in one level's active cells give that
+    level's plain average; a uniform field gives the uniform value
+    everywhere; a field 1 on level-0 cells and 3 on level-1 cells gives, in
+    a ring whose cells are all on one level, 1 or 3, and in between the
+    area-weighted value (level-1 cells count a quarter)."""
+    from oracle.jetstats import radial_profile_levels
+    N0 = 32
+    act0 = np.ones((N0, N0, 4), dtype=bool)
+    act0[8:24, 8:24, :] = False                      # refined square in the middle
+    act1 = np.zeros((2 * N0, 2 * N0, 8), dtype=bool)
+    act1[16:48, 16:48, :] = True
+    one = lambda a, v: np.where(a, v, np.nan)
+    lv = [(one(act0, 1.0), one(act0, 0.0), act0), (one(act1, 3.0), one(act1, 0.0), act1)]
+    y0 = z0 = 16.2
+    pm, pv, pc = radial_profile_levels(lv, y0, z0, 1.0, 22, [1.3])
+    inner = np.arange(22) < 7          # r < 7: only fine cells (square of half side 8)
+    outer = np.arange(22) >= 12        # r >= 12 (> 8 sqrt 2): only coarse cells
+    ok = pc[0] > 0
+    assert np.allclose(pm[0][inner & ok], 3.0, atol=1e-15)
+    assert np.allclose(pm[0][outer & ok], 1.0, atol=1e-15)
+    mid = ok & ~inner & ~outer
+    assert ((pm[0][mid] > 1.0) & (pm[0][mid] < 3.0)).any()
+    # mixed rings: (n0 * 1 + n1 / 4 * 3) / (n0 + n1 / 4) with n_l the active
+    # cells of level l whose centre lies in the ring (counted on the grids)
+    c0 = np.arange(N0) + 0.5
+    c1 = (np.arange(2 * N0) + 0.5) / 2
+    r0 = np.sqrt((c0[None, :] - y0) ** 2 + (c0[:, None] - z0) ** 2)
+    r1 = np.sqrt((c1[None, :] - y0) ** 2 + (c1[:, None] - z0) ** 2)
+    for b in np.nonzero(mid)[0]:
+        n0 = int((act0[:, :, 1] & (np.floor(r0) == b)).sum())
+        n1 = int((act1[:, :, 2] & (np.floor(r1) == b)).sum())
+        assert abs(pm[0][b] - (n0 + 0.75 * n1) / (n0 + 0.25 * n1)) <= 1e-14
+    # the same rings from the fine level alone (plain averages) where it holds them
+    pf, _, cf = radial_profile(one(act1, 3.0), one(act1, 0.0), 1, y0, z0, 1.0, 22, [1.3])
+    assert np.array_equal(cf[0][inner], pc[0][inner])
+    # a uniform field is uniform whatever the split
+    lu = [(one(act0, 0.02), one(act0, 1e-6), act0), (one(act1, 0.02), one(act1, 1e-6), act1)]
+    um, uv, uc = radial_profile_levels(lu, y0, z0, 1.0, 22, [1.3])
+    assert np.allclose(um[0][uc[0] > 0], 0.02, rtol=1e-14)
+    assert np.allclose(uv[0][uc[0] > 0], 1e-6, rtol=1e-12)
