@@ -103,8 +103,8 @@ typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2 } lbm_storage;
  * x = 0 onto the cap (the solid cell takes f_eq(rho of the fluid cell
  * downstream, u_bc at its own y, z)) and the face x = 0 holds u = 0.  The
  * body lives on one level: the finest whose blocks cover the cylinder grown
- * by two of its cells, each of them a non-refined block whose 26 neighbours
- * are blocks of that level (checked; lbm_plan_info.nozzle_level). */
+ * by two of its cells, each of them and its 26 neighbours being non-refined
+ * blocks of that level (checked; lbm_plan_info.nozzle_level). */
 typedef struct {
   int nbx, nby, nbz;
   int periodic_x;

@@ -29,9 +29,9 @@ upstream cap are no-slip links with the q of their entry point.
 
 The body lies on one level l_n: the finest level whose blocks cover the
 cylinder's bounding box grown by two cells of that level, each such block
-being a non-refined block of level l_n whose 26 neighbours are blocks of
-level l_n (so links and their second cells stay among active cells, away
-from every interface and domain face).
+and its 26 neighbours being non-refined blocks of level l_n (so links and
+their second cells stay among active cells, and no interpolation stencil or
+restriction of an interface reaches the body or a domain face).
 """
 import math
 
@@ -116,7 +116,8 @@ def nozzle_level(levels, geom):
         for bz in range(lo[2], hi[2] + 1):
             for by in range(lo[1], hi[1] + 1):
                 for bx in range(lo[0], hi[0] + 1):
-                    if bool(ref[bz, by, bx]) or not bool(reg[bz - 1:bz + 2, by - 1:by + 2, bx - 1:bx + 2].all()):
+                    nbh = (slice(bz - 1, bz + 2), slice(by - 1, by + 2), slice(bx - 1, bx + 2))
+                    if not bool(reg[nbh].all()) or bool(ref[nbh].any()):
                         ok = False
         if ok:
             return l

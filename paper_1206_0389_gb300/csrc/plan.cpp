@@ -561,7 +561,8 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
   if (nozzle) {
     const double y0 = g.nozzle_y0, z0 = g.nozzle_z0, R = g.nozzle_r, x0 = g.nozzle_x0, x1 = g.nozzle_x1;
     // the finest level whose blocks cover the cylinder grown by two of its
-    // cells, all of them non-refined with their 26 neighbours in the level
+    // cells, all of them and their 26 neighbours non-refined blocks of the
+    // level (no interface stencil reaches the body)
     int ln = -1;
     double box[3][2];
     for (int l = L - 1; l >= 0 && ln < 0; --l) {
@@ -580,11 +581,10 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
       for (int bz = lo[2]; ok && bz <= hi[2]; ++bz)
         for (int by = lo[1]; ok && by <= hi[1]; ++by)
           for (int bx = lo[0]; ok && bx <= hi[0]; ++bx) {
-            if (d.refined[d.at(bx, by, bz)]) ok = false;
             for (int dz = -1; dz <= 1; ++dz)
               for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx)
-                  if (!d.reg(bx + dx, by + dy, bz + dz)) ok = false;
+                  if (!d.reg(bx + dx, by + dy, bz + dz) || d.refined[d.at(bx + dx, by + dy, bz + dz)]) ok = false;
           }
       if (ok) {
         ln = l;

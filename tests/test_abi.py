@@ -183,6 +183,10 @@ def test_plan_nozzle_matches_oracle(model):
     with pytest.raises(lbm.LbmError):
         lbm.lbm_plan((5, 5, 5), False, [], model, "f32", nozzle=(20.0, 20.0, 4.3, 24.0, 10.0))
     assert lbm.lbm_plan((5, 5, 5), False, [], model, "f32").nozzle_level == -1
+    r2 = np.zeros((5, 5, 5), dtype=bool)
+    r2[2, 2, 4] = True                      # refined block next to the level-0 nozzle's blocks
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_plan((5, 5, 5), False, [r2], model, "f32", nozzle=(20.0, 20.0, 4.3, 10.25, 24.0))
 
 
 def test_create_without_gpu_reports_cuda_error():

@@ -153,3 +153,12 @@ def test_nozzle_placement_rules():
         NestedSolver("d3q27", (5, 5, 5), periodic_x=False, refine=[r], nozzle=(20.0, 20.0, 4.3, 10.25, 24.0))
     with pytest.raises(ValueError):           # touches the domain's blocks next to the face
         NestedSolver("d3q27", (5, 5, 5), periodic_x=False, nozzle=(20.0, 20.0, 4.3, 2.25, 24.0))
+
+
+def test_nozzle_next_to_refined_blocks_is_rejected():
+    """A level-0 nozzle whose blocks touch a refined block would put solid
+    cells into the coarse-to-fine stencils: rejected on both sides."""
+    r = torch.zeros(5, 5, 5, dtype=torch.bool)
+    r[2, 2, 4] = True                       # refined block next to the nozzle's blocks (x block 3)
+    with pytest.raises(ValueError):
+        NestedSolver("d3q27", (5, 5, 5), periodic_x=False, refine=[r], nozzle=NOZ)
