@@ -32,11 +32,6 @@ thread_local std::string g_create_error;
 
 struct Op {
   enum Kind { UPDATE, C2F, F2C, BC, LINK, INC } kind;
-  // consecutive ops of one group (> 0) run concurrently in the coarse-step
-  // graph: those with side = true on the second stream, the others on the
-  // main stream in order; the vector order is a valid sequential order
-  int group = 0;
-  bool side = false;
   UpdateArgs ua{};
   C2FArgs ca{};
   F2CArgs fa{};
@@ -182,7 +177,6 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
   const double cs2_3 = 3.0 * c->cs * c->cs;
   const bool les = c->model == LBM_D3Q19_MRT_LES;
   const int K = 1 << (L - 1);
-  int group = 0;
   for (int k = 0; k < K; ++k) {
     int lmin = L - 1;
     for (int l = 0; l < L; ++l)
@@ -193,8 +187,6 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
     auto sub = [&](int l) { return k / (1 << (L - 1 - l)); };
     // coarse-to-fine for every level starting a substep: one launch (level
     // l writes its ghost cells and reads active / hidden-1 cells of l-1)
-    Op c2f_op, bc_op, link_op;
-    c2f_op.kind = bc_op.kind = link_op.kind = Op::INC;  // INC marks "none" here
     if (std::max(lmin, 1) < L) {
       Op op;
       op.kind = Op::C2F;
@@ -235,7 +227,7 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
         v.tau0_f = fp.tau0;
         a.n += v.n;
       }
-      if (a.n > 0) c2f_op = op;
+      if (a.n > 0) ops.push_back(op);
     }
     // inflow / outflow ghosts of the same levels (after the interface: an
     // inflow ghost may take its density from a coarse-to-fine ghost cell)
@@ -265,7 +257,7 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
         v.inv_scale = std::ldexp(1.0, -l);
         b.n += v.n;
       }
-      if (b.n > 0) bc_op = op;
+      if (b.n > 0) ops.push_back(op);
     }
     // nozzle links of its level (after the level's previous update, before
     // this one; they touch only cells near the body)
@@ -288,7 +280,7 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
       a.u_in = c->u_in;
       a.perturb = c->perturb;
       a.seed = c->seed;
-      link_op = op;
+      ops.push_back(op);
     }
     Op up;
     up.kind = Op::UPDATE;
@@ -312,48 +304,7 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
                                        : static_cast<const void*>(c->dl[0].force_f);
     u.walls = c->plan.walls;
     u.slip = c->plan.slip;
-    const bool has_c2f = c2f_op.kind == Op::C2F, has_bc = bc_op.kind == Op::BC, has_link = link_op.kind == Op::LINK;
-    const int64_t n_coarse = lmin + 1 < L ? c->list_len[lmin] - c->list_len[lmin + 1] : 0;
-    if (lmin == 0 && L > 1 && has_c2f && n_coarse > 0 && c->list_len[1] > 0) {
-      // the level-0 update needs no coarse-to-fine ghost: it runs beside the
-      // coarse-to-fine launch (which reads only level-0 cells that this
-      // update reads too, and writes ghosts of the finer levels), and the
-      // finer levels' update follows both
-      ++group;
-      c2f_op.group = group;
-      c2f_op.side = true;
-      ops.push_back(c2f_op);
-      if (has_bc) {
-        bc_op.group = group;
-        ops.push_back(bc_op);
-      }
-      if (has_link && link_op.la.level == 0) {
-        link_op.group = group;
-        ops.push_back(link_op);
-      }
-      Op u0 = up;
-      u0.ua.nitems = int(n_coarse);
-      u0.group = group;
-      ops.push_back(u0);
-      if (has_link && link_op.la.level > 0) ops.push_back(link_op);
-      Op u1 = up;
-      u1.ua.items = c->items + c->list_off[1];
-      u1.ua.nitems = int(c->list_len[1]);
-      ops.push_back(u1);
-    } else {
-      // the inflow launch touches cells other than the coarse-to-fine
-      // launch's (inflow ghosts fed by ghost cells are written by the
-      // latter): the two run side by side
-      if (has_c2f && has_bc) {
-        ++group;
-        c2f_op.group = bc_op.group = group;
-        bc_op.side = true;
-      }
-      if (has_c2f) ops.push_back(c2f_op);
-      if (has_bc) ops.push_back(bc_op);
-      if (has_link) ops.push_back(link_op);
-      ops.push_back(up);
-    }
+    ops.push_back(up);
     for (int l = lmin; l < L; ++l) par[l] ^= 1;
     // fine-to-coarse after the second substep of each fine level: one launch
     // (level l-1's hidden cells take level l's active cells, which no other
@@ -448,24 +399,23 @@ int build_graphs(lbm_ctx* ctx) {
     cudaError_t e = cudaSuccess;
     size_t ev = 0;
     for (size_t k = 0; k < ops.size() && e == cudaSuccess; ++k) {
-      const int g = ops[k].group;
-      if (g == 0 || ev + 1 >= ctx->fork_join.size()) {
-        e = run_op(ctx, ops[k]);
+      // the inflow launch after a coarse-to-fine launch touches other cells
+      // (inflow ghosts fed by ghost cells are written by the latter), so the
+      // graph runs the two side by side
+      if (ops[k].kind == Op::C2F && k + 1 < ops.size() && ops[k + 1].kind == Op::BC &&
+          ev + 1 < ctx->fork_join.size()) {
+        cudaEvent_t fork = ctx->fork_join[ev++], join = ctx->fork_join[ev++];
+        if ((e = cudaEventRecord(fork, ctx->stream)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->side, fork, 0)) != cudaSuccess ||
+            (e = run_op(ctx, ops[k + 1], ctx->side)) != cudaSuccess ||
+            (e = run_op(ctx, ops[k], ctx->stream)) != cudaSuccess ||
+            (e = cudaEventRecord(join, ctx->side)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->stream, join, 0)) != cudaSuccess)
+          break;
+        ++k;
         continue;
       }
-      // a group: fork the side stream, run each op on its stream, join
-      size_t k1 = k;
-      while (k1 + 1 < ops.size() && ops[k1 + 1].group == g) ++k1;
-      cudaEvent_t fork = ctx->fork_join[ev++], join = ctx->fork_join[ev++];
-      if ((e = cudaEventRecord(fork, ctx->stream)) != cudaSuccess ||
-          (e = cudaStreamWaitEvent(ctx->side, fork, 0)) != cudaSuccess)
-        break;
-      for (size_t j = k; j <= k1 && e == cudaSuccess; ++j)
-        e = run_op(ctx, ops[j], ops[j].side ? ctx->side : ctx->stream);
-      if (e != cudaSuccess || (e = cudaEventRecord(join, ctx->side)) != cudaSuccess ||
-          (e = cudaStreamWaitEvent(ctx->stream, join, 0)) != cudaSuccess)
-        break;
-      k = k1;
+      e = run_op(ctx, ops[k]);
     }
     cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
     if (e != cudaSuccess) {
