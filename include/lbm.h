@@ -214,8 +214,10 @@ int lbm_stats_get(lbm_ctx* ctx, int level, double* mean, double* var, int64_t* n
  * every level of a nested grid: the unrefined cells of each level l in its
  * layer containing x, weighted by their cross-section area 4^-l (they tile
  * the plane), the values being area-weighted ring averages.  Arrays are
- * [nstations][nbins].  LBM_ERR_STATE before any sample; LBM_ERR_ARG for a
- * station outside the level or dr <= 0. */
+ * [nstations][nbins].  The ring sums are float64 atomics, so their order
+ * (and the last bit of a ring's value) may vary between calls.
+ * LBM_ERR_STATE before any sample; LBM_ERR_ARG for a station outside the
+ * level or dr <= 0. */
 int lbm_stats_radial(lbm_ctx* ctx, int level, double y0, double z0, double dr, int nbins, int nstations,
                      const double* x, double* mean_ux, double* var_ux, int64_t* counts);
 
