@@ -47,7 +47,10 @@ f~_opp(i)(x, t) (the wall lies half a cell outside the boundary cells); at a
 free-slip face by specular reflection, the population with the wall-normal
 velocity component flipped, pulled from the same layer, f_i(x, t+1) =
 f~_m(i)(x - e_i + (e_i . n) n, t).  Where a link crosses two walls, a no-slip
-crossing wins; two free-slip crossings reflect both components.
+crossing wins; two free-slip crossings reflect both components.  With x not
+periodic, the face x = 0 (bit 4) and the face x = NX (bit 5) may be no-slip
+walls too (the tank's upstream wall behind the nozzle; a closed box): they
+replace the inflow or the outflow for the populations entering through them.
 
 Pressure outlet (Section 3.2 replaces the tank's weir by a fixed pressure; the
 scheme is not given): with outlet = 1 the ghost column x = NX of level 0
@@ -73,7 +76,8 @@ class NestedSolver:
     def __init__(self, model, nb, periodic_x=True, refine=(), omega=1.0, cs=0.0, walls=0, slip=0,
                  outlet=0, nozzle=None, body=None):
         """walls: bit 0/1 the low/high y face, bit 2/3 the low/high z face are
-        walls (both faces of an axis or neither); slip: the same bits mark the
+        walls (both faces of an axis or neither), bit 4/5 the faces x = 0 and
+        x = NX are no-slip walls (non-periodic x); slip: the y/z bits mark the
         free-slip walls among them (the others are no-slip).  outlet: 0
         zero-gradient outflow, 1 fixed-pressure outlet (non-periodic x).
         nozzle: (y0, z0, R, x0, x1) of the nozzle cylinder (oracle/nozzle.py),
@@ -81,8 +85,12 @@ class NestedSolver:
         grid (the pins' plane walls)."""
         self.m = Model(model)
         self.Q = self.m.Q
-        if (walls & 3) not in (0, 3) or (walls & 12) not in (0, 12) or (walls & ~15) or (slip & ~walls):
-            raise ValueError("walls come in pairs per axis; slip marks a subset of them")
+        if (walls & 3) not in (0, 3) or (walls & 12) not in (0, 12) or (walls & ~63) or (slip & ~(walls & 15)):
+            raise ValueError("y/z walls come in pairs per axis; slip marks a subset of them")
+        if (walls & 48) and periodic_x:
+            raise ValueError("x walls need a non-periodic x axis")
+        if (walls & 32) and outlet:
+            raise ValueError("the face x = NX is either a wall or the pressure outlet")
         self.walls, self.slip = int(walls), int(slip)
         if outlet not in (0, 1) or (outlet and periodic_x):
             raise ValueError("outlet is 0 (zero-gradient) or 1 (fixed pressure, non-periodic x)")
@@ -98,6 +106,10 @@ class NestedSolver:
                 near[:, 0, :] = near[:, -1, :] = True
             if walls & 12:
                 near[0] = near[-1] = True
+            if walls & 16:
+                near[:, :, 0] = True
+            if walls & 32:
+                near[:, :, -1] = True
             if bool((r0 & near).any()):
                 raise ValueError("refined blocks must keep one block away from the walls")
         self.levels = build_levels(nb, periodic_x, refine)
@@ -264,10 +276,12 @@ class NestedSolver:
     def _wall_pulls(self, f, pre):
         """Replace the pulls that cross a wall face of level 0 (see the
         module docstring)."""
-        NZ, NY = f.shape[1], f.shape[2]
+        NZ, NY, NXp = f.shape[1], f.shape[2], f.shape[3]
         zz = torch.arange(NZ).reshape(NZ, 1, 1)
         yy = torch.arange(NY).reshape(1, NY, 1)
+        xx = torch.arange(NXp).reshape(1, 1, NXp)
         W, S = self.walls, self.slip
+        x_lo, x_hi = 1, NXp - 2                       # padded indices of x = 0 and x = NX - 1
         for q in range(self.Q):
             ex, ey, ez = (int(v) for v in self.m.e[q])
             cy = torch.zeros((1, NY, 1), dtype=torch.bool)
@@ -281,10 +295,15 @@ class NestedSolver:
                 cz, slip_z = zz == 0, bool(S & 4)
             if ez == -1 and W & 8:
                 cz, slip_z = zz == NZ - 1, bool(S & 8)
-            cross = (cy | cz).expand(pre[q].shape)
+            cx = torch.zeros((1, 1, NXp), dtype=torch.bool)
+            if ex == 1 and W & 16:
+                cx = xx == x_lo
+            if ex == -1 and W & 32:
+                cx = xx == x_hi
+            cross = (cy | cz | cx).expand(pre[q].shape)
             if not bool(cross.any()):
                 continue
-            noslip = ((cy & (not slip_y)) | (cz & (not slip_z))).expand(pre[q].shape)
+            noslip = ((cy & (not slip_y)) | (cz & (not slip_z)) | cx).expand(pre[q].shape)
             both = (cy & cz).expand(pre[q].shape)
             only_y = (cy & ~cz).expand(pre[q].shape)
             bounce = f[self._vel_index(-ex, -ey, -ez)]

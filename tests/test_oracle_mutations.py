@@ -144,6 +144,7 @@ def test_bounce_back_without_reversal_is_caught(monkeypatch):
     S_orig_wall = S.NestedSolver._wall_pulls
     monkeypatch.setattr(S.NestedSolver, "_wall_pulls", wall_pulls)
     assert fails(TW.test_no_slip_poiseuille_profile)
+    assert fails(TW.test_x_walls_hold_poiseuille_profile)
 
 
 def test_free_slip_flipping_the_tangential_component_is_caught(monkeypatch):

@@ -78,3 +78,56 @@ def test_walls_reject_refinement_next_to_them():
         NestedSolver("d3q27", (2, 2, 2), refine=[r], walls=3)
     with pytest.raises(ValueError):
         NestedSolver("d3q27", (2, 2, 2), walls=1)
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("slip", [0, 12, 3])
+def test_closed_box_conserves_mass(model, slip):
+    """All six faces walls (x faces no-slip, y/z mixed): the mass of a
+    far-from-equilibrium state is conserved to round-off."""
+    s = NestedSolver(model, (2, 1, 2), periodic_x=False, omega=1.6, cs=0.1 if model == "d3q19" else 0.0,
+                     walls=63, slip=slip)
+    lv = s.levels[0]
+    f = torch.from_numpy(random_state(model, (lv.NX, lv.NY, lv.NZ), 17, 0.2))
+    s.set_state(0, f)
+    m0 = s.state(0).sum().item()
+    s.step(5)
+    assert abs(s.state(0).sum().item() - m0) <= 1e-12 * f.numel()
+
+
+def test_x_walls_hold_poiseuille_profile():
+    """Body-force-driven flow along y between no-slip walls at x = 0 and
+    x = NX (half a cell outside the boundary cells): the parabola
+    u_y(x) = F / (2 nu) (x + 1/2) (NX - 1/2 - x) is kept within 1 % of its
+    maximum over 200 steps."""
+    NX, tau, umax = 16, 0.8, 0.01
+    nu = (tau - 0.5) / 3
+    F = 8 * nu * umax / NX ** 2
+    s = NestedSolver("d3q27", (2, 1, 1), periodic_x=False, omega=1 / tau, walls=48)
+    lv = s.levels[0]
+    x = torch.arange(NX, dtype=DTYPE)
+    uy = F / (2 * nu) * (x + 0.5) * (NX - 0.5 - x)
+    u = torch.zeros(3, lv.NZ, lv.NY, lv.NX, dtype=DTYPE)
+    u[1] = uy[None, None, :]
+    s.init_equilibrium(0, None, u)
+    Fv = torch.zeros(3, lv.NZ, lv.NY, lv.NX, dtype=DTYPE)
+    Fv[1] = F
+    s.set_force(Fv)
+    s.step(200)
+    _, uu = s.macroscopic(0)
+    assert (uu[1] - uy[None, None, :]).abs().max().item() <= 0.01 * umax
+    assert uu[0].abs().max().item() <= 1e-6 * umax
+
+
+def test_x_wall_rules():
+    with pytest.raises(ValueError):
+        NestedSolver("d3q27", (2, 1, 1), periodic_x=True, walls=16)
+    with pytest.raises(ValueError):
+        NestedSolver("d3q27", (2, 1, 1), periodic_x=False, walls=32, outlet=1)
+    with pytest.raises(ValueError):
+        NestedSolver("d3q27", (2, 1, 1), periodic_x=False, walls=16, slip=16)
+    r = torch.zeros(2, 2, 3, dtype=torch.bool)
+    r[:, :, 0] = True
+    with pytest.raises(ValueError):
+        NestedSolver("d3q27", (3, 2, 2), periodic_x=False, refine=[r], walls=16)
+    NestedSolver("d3q27", (3, 2, 2), periodic_x=False, refine=[r], walls=32)
