@@ -70,15 +70,18 @@ typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2 } lbm_storage;
  *
  * Walls (Section 3.2: the tank's no-slip walls and free-slip top): walls has
  * bit 0/1 for the low/high y face and bit 2/3 for the low/high z face; the
- * faces of an axis are walls together or not at all (3, 12 or 15 when set).
- * slip marks the free-slip walls among them (a subset of walls); the others
- * are no-slip.  A pull that would cross a wall face is reflected: no-slip by
+ * faces of y or z are walls together or not at all.  slip marks the
+ * free-slip walls among them (a subset of those bits); the others are
+ * no-slip.  With a non-periodic x, bit 4 makes the face x = 0 and bit 5 the
+ * face x = NX a no-slip wall (the tank's upstream wall behind the nozzle, a
+ * closed box); they replace the inflow / outflow for the populations
+ * entering there, and bit 5 excludes the pressure outlet.  A pull that would cross a wall face is reflected: no-slip by
  * half-way bounce-back, f_i(x, t+1) = f~_opp(i)(x, t) (the wall lies half a
  * cell outside the boundary cells); free-slip by specular reflection, the
  * population with its wall-normal components flipped pulled along the other
  * axes, f_i(x, t+1) = f~_m(i)(x - e_i + (e_i . n) n, t).  A no-slip crossing
  * wins over a free-slip one; two free-slip crossings flip both components.
- * Refined level-0 blocks must keep one block away from the wall faces
+ * Refined level-0 blocks must keep one block away from every wall face
  * (checked).  walls = slip = 0 (a zero-initialised struct) keeps y and z
  * periodic.
  *

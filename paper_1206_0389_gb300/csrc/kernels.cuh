@@ -16,7 +16,9 @@ constexpr int kMaxL = LBM_MAX_LEVELS;
 // edges: bit 2a (2a+1) set when the block sits on the low (high) face of a
 // level box that wraps periodically along axis a (x, y, z); bit 6 set when
 // its +x face is the zero-gradient outflow x = NX (the populations entering
-// through it are pulled from the cell x = NX - 1 itself).
+// through it are pulled from the cell x = NX - 1 itself); bit 7 set for a
+// level-0 block whose -x face is the domain face x = 0 when that face is a
+// wall.
 struct WorkItem {
   int32_t block;
   uint8_t level;
@@ -52,8 +54,9 @@ struct UpdateArgs {
   double cs2_18;          // 18 Cs^2
   const void* force;      // level 0 body force [3][nblocks*512] (block order) in the
                           // compute type (double for F64 storage, else float) or nullptr
-  int walls, slip;        // level-0 wall faces (bit 0/1 low/high y, 2/3 low/high z) and
-                          // the free-slip ones among them; read by the W = true kernels
+  int walls, slip;        // level-0 wall faces (bit 0/1 low/high y, 2/3 low/high z, 4/5
+                          // the faces x = 0 / x = NX, no-slip) and the free-slip ones
+                          // among the y/z walls; read by the W = true kernels
 };
 
 // coarse-to-fine work comes in chunks of consecutive ghost cells (sorted by

@@ -72,8 +72,10 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
   if (g.levels < 1 || g.levels > kMaxL) return "levels must be in 1..4";
   if (g.levels > 1 && g.refine == nullptr) return "refine flags required when levels > 1";
   if (!(omega > 0.0 && omega < 2.0)) return "omega must be in (0, 2)";
-  if ((g.walls & 3) % 3 != 0 || (g.walls & 12) % 12 != 0 || (g.walls & ~15) || (g.slip & ~g.walls))
-    return "walls come in pairs per axis (bits 0|1 for y, 2|3 for z); slip must be a subset of walls";
+  if ((g.walls & 3) % 3 != 0 || (g.walls & 12) % 12 != 0 || (g.walls & ~63) || (g.slip & ~(g.walls & 15)))
+    return "y/z walls come in pairs per axis (bits 0|1 for y, 2|3 for z); slip must be a subset of them";
+  if ((g.walls & 48) && g.periodic_x) return "x walls (bits 4, 5) need a non-periodic x axis";
+  if ((g.walls & 32) && g.outlet) return "the face x = NX is either a wall or the pressure outlet";
   if (g.outlet != 0 && g.outlet != 1) return "outlet must be 0 (zero-gradient) or 1 (fixed pressure)";
   if (g.outlet && g.periodic_x) return "a pressure outlet needs a non-periodic x axis";
   const bool nozzle = g.nozzle_r > 0;
@@ -127,7 +129,9 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
           for (int by = 0; by < d.nby; ++by)
             for (int bx = 0; bx < d.nbx; ++bx)
               if (d.refined[d.at(bx, by, bz)] && (((g.walls & 3) && (by == 0 || by == d.nby - 1)) ||
-                                                  ((g.walls & 12) && (bz == 0 || bz == d.nbz - 1)))) {
+                                                  ((g.walls & 12) && (bz == 0 || bz == d.nbz - 1)) ||
+                                                  ((g.walls & 16) && bx == 0) ||
+                                                  ((g.walls & 32) && bx == d.nbx - 1))) {
                 snprintf(msg, sizeof msg, "refined block (%d,%d,%d) touches a wall face", bx, by, bz);
                 return msg;
               }
@@ -284,7 +288,8 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
           w.edges = uint8_t((lp.wrap[0] && X == 0 ? 1 : 0) | (lp.wrap[0] && X == lp.BX - 1 ? 2 : 0) |
                             (lp.wrap[1] && Y == 0 ? 4 : 0) | (lp.wrap[1] && Y == lp.BY - 1 ? 8 : 0) |
                             (lp.wrap[2] && Z == 0 ? 16 : 0) | (lp.wrap[2] && Z == lp.BZ - 1 ? 32 : 0) |
-                            (!px && !P.outlet && bx == d.nbx - 1 ? 64 : 0));
+                            (!px && !P.outlet && bx == d.nbx - 1 ? 64 : 0) |
+                            (l == 0 && (P.walls & 16) && bx == 0 ? 128 : 0));
           if (!d.refined[i]) {
             std::fill(k, k + 512, uint8_t(K_ACTIVE));
             lp.active_cells += 512;

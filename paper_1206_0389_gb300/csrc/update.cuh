@@ -17,8 +17,8 @@
 // (NX - 1, y', z') is read from that cell directly.
 //
 // Walls (instances with W = true): a pull of a level-0 cell that would cross
-// a y or z wall face of the domain is replaced after the periodic pull, for
-// the cells next to a wall only.  No-slip (half-way
+// a wall face of the domain (y, z, or the no-slip x faces) is replaced after
+// the periodic pull, for the cells next to a wall only.  No-slip (half-way
 // bounce-back): f_i(x) = f~_opp(i)(x), the opposite population of the cell
 // itself.  Free-slip (specular reflection): the population with the
 // wall-normal components flipped, pulled along the axes not crossed only,
@@ -75,8 +75,12 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
     const int dzm = (w.edges & 16) ? BXY * (L.BZ - 1) : -BXY;
     const int dzp = (w.edges & 32) ? -BXY * (L.BZ - 1) : BXY;
     // wall faces this block touches (bit 0/1 low/high y, 2/3 low/high z):
-    // the level-0 box is the domain, so its wrapping faces are the walls
-    const int wf = (W && w.level == 0) ? (a.walls & ((w.edges >> 2) & 15)) : 0;
+    // the level-0 box spans the domain in y and z, so its wrapping faces
+    // are the walls; the x faces come from edges bits 7 (x = 0) and 6 (the
+    // face x = NX, whose fused outflow read the fix-up then replaces)
+    const int wf = (W && w.level == 0)
+                       ? (a.walls & (((w.edges >> 2) & 15) | ((w.edges & 128) ? 16 : 0) | ((w.edges & 64) ? 32 : 0)))
+                       : 0;
     const T tau0 = T(L.tau0);
     const S* __restrict__ src = reinterpret_cast<const S*>(L.src) + int64_t(w.block) * QS;
     S* __restrict__ dst = reinterpret_cast<S*>(L.dst) + int64_t(w.block) * QS;
@@ -116,19 +120,21 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
     // replaces, for a cell next to a wall face, the populations whose pull
     // crossed it (the periodic pull above read a valid but unused value)
     auto wall_fix = [&](int c, T (&g)[Q]) {
-      const int y = (c >> 3) & 7, z = c >> 6;
+      const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
       const bool yl = (wf & 1) && y == 0, yh = (wf & 2) && y == 7;
       const bool zl = (wf & 4) && z == 0, zh = (wf & 8) && z == 7;
-      if (!(yl || yh || zl || zh)) return;
+      const bool xl = (wf & 16) && x == 0, xh = (wf & 32) && x == 7;
+      if (!(yl || yh || zl || zh || xl || xh)) return;
       int Xm, Xp, Ym, Yp, Zm, Zp;
       offsets(c, Xm, Xp, Ym, Yp, Zm, Zp);
       const S* p = src + c;
       static_for<Q>([&](auto i) {
         constexpr int ex = Lattice<Q>::ex(i), ey = Lattice<Q>::ey(i), ez = Lattice<Q>::ez(i);
-        if constexpr (ey != 0 || ez != 0) {
+        if constexpr (ex != 0 || ey != 0 || ez != 0) {
           const bool cy = ey == 1 ? yl : ey == -1 ? yh : false;
           const bool cz = ez == 1 ? zl : ez == -1 ? zh : false;
-          if (cy || cz) {
+          const bool cx = ex == 1 ? xl : ex == -1 ? xh : false;  // x walls are no-slip
+          if (cy || cz || cx) {
             const bool sy = a.slip & (ey == 1 ? 1 : 2), sz = a.slip & (ez == 1 ? 4 : 8);
             const int X = ex == 1 ? Xm : ex == -1 ? Xp : 0;
             const int Y = ey == 1 ? Ym : ey == -1 ? Yp : 0;
@@ -138,7 +144,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
             constexpr int iz = Lattice<Q>::index(ex, ey, -ez);
             constexpr int iyz = Lattice<Q>::index(ex, -ey, -ez);
             int o;
-            if ((cy && !sy) || (cz && !sz)) o = ib * kCells;
+            if (cx || (cy && !sy) || (cz && !sz)) o = ib * kCells;
             else if (cy && cz) o = iyz * kCells - ex + X;
             else if (cy) o = iy * kCells - (ex + 64 * ez) + X + Z;
             else o = iz * kCells - (ex + 8 * ey) + X + Y;

@@ -99,22 +99,25 @@ def test_plan_rejects_bad_grids():
         lbm.lbm_plan((0, 2, 2), True, [])
 
 
-@pytest.mark.parametrize("walls,slip,ok", [(0, 0, True), (3, 0, True), (12, 12, True), (15, 9, True),
-                                            (1, 0, False), (6, 0, False), (3, 4, False), (16, 0, False)])
-def test_plan_wall_rules_match_oracle(walls, slip, ok):
-    """Walls come in pairs per axis and slip is a subset of them: the planner
-    and the oracle accept and reject the same settings."""
+@pytest.mark.parametrize("walls,slip,px,ok", [(0, 0, True, True), (3, 0, True, True), (12, 12, True, True),
+                                               (15, 9, True, True), (1, 0, True, False), (6, 0, True, False),
+                                               (3, 4, True, False), (16, 0, True, False), (16, 0, False, True),
+                                               (63, 12, False, True), (48, 16, False, False), (64, 0, False, False)])
+def test_plan_wall_rules_match_oracle(walls, slip, px, ok):
+    """y/z walls come in pairs per axis, slip is a subset of them, x walls
+    need a non-periodic x: the planner and the oracle accept and reject the
+    same settings."""
     try:
-        NestedSolver("d3q27", (2, 2, 2), walls=walls, slip=slip)
+        NestedSolver("d3q27", (2, 2, 2), periodic_x=px, walls=walls, slip=slip)
         oracle_ok = True
     except ValueError:
         oracle_ok = False
     assert oracle_ok == ok
     if ok:
-        lbm.lbm_plan((2, 2, 2), True, [], walls=walls, slip=slip)
+        lbm.lbm_plan((2, 2, 2), px, [], walls=walls, slip=slip)
     else:
         with pytest.raises(lbm.LbmError):
-            lbm.lbm_plan((2, 2, 2), True, [], walls=walls, slip=slip)
+            lbm.lbm_plan((2, 2, 2), px, [], walls=walls, slip=slip)
 
 
 def test_plan_rejects_refinement_next_to_walls():

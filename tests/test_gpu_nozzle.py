@@ -141,13 +141,15 @@ def test_nozzle_keeps_rest_and_rejects_bad_placement():
 
 
 @pytest.mark.parametrize("model", MODELS)
-def test_paper_tank_all_boundaries_f64(model):
+@pytest.mark.parametrize("walls", [15, 31])
+def test_paper_tank_all_boundaries_f64(model, walls):
     """The paper's tank on a small nested grid: no-slip side walls and
     bottom, free-slip top, pressure outlet, the nozzle on the fine level with
-    the inflow on its cap; two coarse steps against the oracle."""
+    the inflow on its cap, with or without the upstream wall at x = 0; two
+    coarse steps against the oracle."""
     lbm = gpu()
     nb, ref = nested_grid()
-    ctx, orc = pair(model, "f64", nb, ref, nozzle=NOZ1, walls=15, slip=8, outlet=1)
+    ctx, orc = pair(model, "f64", nb, ref, nozzle=NOZ1, walls=walls, slip=8, outlet=1)
     lbm.lbm_set_outlet(ctx, 0.998)
     orc.set_outlet(0.998)
     fields = [synth.taylor_green_3d(lv.NY, 0.02, shape=(lv.NX, lv.NY, lv.NZ)) for lv in orc.levels]

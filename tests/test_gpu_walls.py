@@ -203,3 +203,33 @@ def test_walls_reject_bad_settings_and_the_adjoint():
         lbm.lbm_adjoint_forward(ctx, 4, 2)
     assert e.value.status == lbm.LBM_ERR_STATE
     lbm.lbm_destroy(ctx)
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("walls,slip", [(63, 0), (63, 12), (48, 0), (31, 8)])
+@pytest.mark.parametrize("variant", ["128,1,0", "128,7,0"])
+def test_x_walls_f64(model, walls, slip, variant, monkeypatch):
+    """No-slip walls on the x faces (a closed box with mixed y/z walls, a
+    channel between x walls, the tank's upstream wall with an open outflow):
+    two steps from a random state against the oracle."""
+    monkeypatch.setenv("LBM_LAUNCH_SHAPE", variant)
+    nb = (3, 2, 2)
+    ctx, orc = make_pair(model, "f64", nb, False, omega=1.7, cs=0.18, walls=walls, slip=slip)
+    upload_same_state(ctx, orc, [random_state(model, dims(nb), 37, 0.3)])
+    gpu().lbm_step(ctx, 2)
+    orc.step(2)
+    d, _ = compare_levels(ctx, orc)
+    assert d <= 1e-12, d
+    gpu().lbm_destroy(ctx)
+
+
+def test_closed_box_conserves_mass_f64():
+    lbm = gpu()
+    nb = (2, 2, 2)
+    ctx = lbm.lbm_create("d3q27", "f64", nb, False, [], 1.5, 0.0, walls=63, slip=8)
+    lbm.lbm_set_state(ctx, 0, random_state("d3q27", dims(nb), 41, 0.1))
+    m0 = lbm.lbm_mass_momentum(ctx)[0]
+    lbm.lbm_step(ctx, 100)
+    m1 = lbm.lbm_mass_momentum(ctx)[0]
+    assert abs(m1 - m0) <= 1e-11 * abs(m0)
+    lbm.lbm_destroy(ctx)
