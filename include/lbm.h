@@ -241,7 +241,9 @@ int lbm_jet_fit(int nbins, double dr, const double* mean_ux, const double* var_u
 int lbm_mass_momentum(lbm_ctx* ctx, double out[4]);
 
 /* Dense float64 copy of a level's distributions, count = Q*NX*NY*NZ doubles.
- * Cells outside the level's blocks read NaN.  The stored (shifted) values are
+ * Cells outside the level's blocks read NaN; cells inside the nozzle hold the
+ * values its links last wrote (no fluid state; lbm_macroscopic gives NaN
+ * there).  The stored (shifted) values are
  * read exactly; for D3Q27 the unshifted sum f = (f - w) + w can round away
  * the lowest bits of a deviation far below w, so use the raw state below for
  * bit-exact checkpoints. */
