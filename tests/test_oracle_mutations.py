@@ -265,3 +265,21 @@ def test_half_width_at_half_maximum_is_caught(monkeypatch):
     monkeypatch.setattr(J, "math", fake)
     assert fails(TJ.test_gaussian_profile_gives_its_width_and_unit_fit)
     assert fails(TJ.test_parabolic_profile_half_width_closed_form)
+
+
+def test_bouzidi_fraction_from_the_solid_side_is_caught(monkeypatch):
+    """The wall fraction measured from the solid cell (1 - q instead of q)."""
+    from oracle import nozzle as N
+    from tests import test_oracle_nozzle as TZ
+    orig = N.Body.wall_values
+
+    def wall_values(self, f):
+        q = self.q
+        self.q = 1.0 - q
+        try:
+            return orig(self, f)
+        finally:
+            self.q = q
+    monkeypatch.setattr(N.Body, "wall_values", wall_values)
+    assert fails(TZ.test_plane_walls_at_any_position_hold_poiseuille, 2.3, 5.2)
+    assert fails(TZ.test_plane_walls_at_any_position_hold_poiseuille, 1.6, 4.45)
