@@ -226,3 +226,29 @@ def test_jet_fit_matches_oracle_on_the_host():
                 assert (math.isnan(a) and math.isnan(b)) or abs(a - b) <= 1e-12 * max(1.0, abs(a))
     empty = lbm.lbm_jet_fit(np.full(5, np.nan), np.full(5, np.nan), np.zeros(5, dtype=np.int64), 1.0)
     assert all(math.isnan(v) for v in empty)
+
+
+def test_plan_nozzle_random_placements_match_oracle():
+    """Random nozzle placements (radius, ends and axis off the cell lattice):
+    the planner and the oracle agree on the level, the solid cells and the
+    number of links, or both reject the placement."""
+    rng = np.random.default_rng(20)
+    agree = 0
+    for _ in range(12):
+        R = float(rng.uniform(1.2, 6.0))
+        y0, z0 = (float(v) for v in rng.uniform(17.0, 23.0, size=2))
+        x0 = float(rng.uniform(9.0, 14.0))
+        x1 = float(rng.uniform(x0 + 2.0, 30.0))
+        noz = (y0, z0, R, x0, x1)
+        try:
+            s = NestedSolver("d3q19", (5, 5, 5), periodic_x=False, nozzle=noz)
+        except ValueError:
+            with pytest.raises(lbm.LbmError):
+                lbm.lbm_plan((5, 5, 5), False, [], "d3q19", "f32", nozzle=noz)
+            continue
+        info = lbm.lbm_plan((5, 5, 5), False, [], "d3q19", "f32", nozzle=noz)
+        assert info.nozzle_level == s.body.l
+        assert info.solid_cells == int(s.body.solid.sum())
+        assert info.nozzle_links == len(s.body.q)
+        agree += 1
+    assert agree >= 4
