@@ -276,8 +276,10 @@ __global__ void k_radial(const RadialArgs a) {
   if (k != K_ACTIVE && (a.active_only || (k != K_HIDDEN1 && k != K_HIDDEN2))) return;
   const double dy = (y + 0.5) * a.inv_scale - a.y0, dz = (z + 0.5) * a.inv_scale - a.z0;
   const double r = sqrt(__dadd_rn(__dmul_rn(dy, dy), __dmul_rn(dz, dz)));
-  const int b = int(floor(r / a.dr));
-  if (b >= a.nbins) return;
+  // compare before converting: r / dr may exceed the int range (tiny dr)
+  const double rb = floor(r / a.dr);
+  if (!(rb < double(a.nbins))) return;
+  const int b = int(rb);
   const int64_t nn = int64_t(a.BX) * a.BY * a.BZ * kCells;
   const double m = a.sums[nn + j] * a.scale;
   const double v = a.sums[4 * nn + j] * a.scale - m * m;
