@@ -79,9 +79,11 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
   if (g.outlet != 0 && g.outlet != 1) return "outlet must be 0 (zero-gradient) or 1 (fixed pressure)";
   if (g.outlet && g.periodic_x) return "a pressure outlet needs a non-periodic x axis";
   const bool nozzle = g.nozzle_r > 0;
-  if (nozzle && !(std::isfinite(g.nozzle_y0) && std::isfinite(g.nozzle_z0) && std::isfinite(g.nozzle_r) &&
-                  std::isfinite(g.nozzle_x0) && std::isfinite(g.nozzle_x1) && g.nozzle_x0 < g.nozzle_x1))
-    return "nozzle: finite values with x0 < x1 required";
+  // (the bound keeps every level's cell coordinates of the nozzle in the int range)
+  auto modest = [](double v) { return std::isfinite(v) && std::fabs(v) < 1e6; };
+  if (nozzle && !(modest(g.nozzle_y0) && modest(g.nozzle_z0) && modest(g.nozzle_r) && modest(g.nozzle_x0) &&
+                  modest(g.nozzle_x1) && g.nozzle_x0 < g.nozzle_x1))
+    return "nozzle: finite values below 1e6 in magnitude with x0 < x1 required";
   const int L = g.levels;
   const int64_t top = int64_t(g.nbx) * g.nby * g.nbz << (3 * (L - 1));
   if (int64_t(g.nbx) << (L - 1) > (1 << 20) || int64_t(g.nby) << (L - 1) > (1 << 20) ||

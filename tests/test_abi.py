@@ -185,6 +185,9 @@ def test_plan_nozzle_matches_oracle(model):
         lbm.lbm_plan((5, 5, 5), False, [r], model, "f32", nozzle=(20.0, 20.0, 4.3, 10.25, 24.0))
     with pytest.raises(lbm.LbmError):
         lbm.lbm_plan((5, 5, 5), False, [], model, "f32", nozzle=(20.0, 20.0, 4.3, 24.0, 10.0))
+    for bad in ((20.0, 20.0, 4.3, 10.0, 1e300), (float("nan"), 20.0, 4.3, 10.0, 20.0), (20.0, 20.0, 1e7, 10.0, 20.0)):
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_plan((5, 5, 5), False, [], model, "f32", nozzle=bad)
     assert lbm.lbm_plan((5, 5, 5), False, [], model, "f32").nozzle_level == -1
     r2 = np.zeros((5, 5, 5), dtype=bool)
     r2[2, 2, 4] = True                      # refined block next to the level-0 nozzle's blocks
