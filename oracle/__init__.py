@@ -17,15 +17,18 @@ collision  D3Q19 MRT + Smagorinsky (Eqs. MRT, relaxationTau, eqSmago,
            eqTauTotFinal, EqnQ; Table 1) and D3Q27 factorized cascaded
            collision by the central-moment definition (Table 2)
 grid       cell masks of the block-structured, 2:1 nested grid
-solver     streaming, boundary ghosts, coarse-to-fine / fine-to-coarse
-           interface transfer and the time-nested schedule
+solver     streaming, boundary ghosts (inflow, zero-gradient or pressure
+           outlet), walls (no-slip / free-slip), coarse-to-fine /
+           fine-to-coarse interface transfer and the time-nested schedule
+nozzle     the nozzle cylinder: solid cells, Bouzidi interpolated no-slip
+           links and the inflow on its cap (Section 3.2)
+jetstats   ring profiles, centreline velocity, half width, turbulence
+           intensity and Gaussian fit of time averages (Section 3.3)
 rng        SplitMix64 counter hash used for the inflow perturbation
 adjoint    reference gradient of a loss w.r.t. a body force (autograd of
            the forward oracle)
 
-Parity status: every function here is pinned by ``tests/test_oracle_*.py``
-except the jet statistics, which the paper only reports as plots
-(parity unpinned for those; they are not part of this package).
+Parity status: every function here is pinned by ``tests/test_oracle_*.py``.
 """
 import torch
 
