@@ -217,6 +217,7 @@ def test_bouzidi_with_q_fixed_at_one_half_is_caught(monkeypatch):
             self.q = q
     monkeypatch.setattr(N.Body, "wall_values", wall_values)
     assert fails(TZ.test_plane_walls_at_any_position_hold_poiseuille, 2.3, 5.2)
+    assert fails(TZ.test_shear_wave_between_interpolated_walls_decays_at_the_true_width, "d3q19", 2.3, 5.2)
 
 
 def test_bouzidi_with_one_branch_for_all_q_is_caught(monkeypatch):
