@@ -145,6 +145,7 @@ def test_bounce_back_without_reversal_is_caught(monkeypatch):
     monkeypatch.setattr(S.NestedSolver, "_wall_pulls", wall_pulls)
     assert fails(TW.test_no_slip_poiseuille_profile)
     assert fails(TW.test_x_walls_hold_poiseuille_profile)
+    assert fails(TW.test_shear_mode_between_no_slip_walls_decays_at_the_channel_rate, "d3q19", 3, 0)
 
 
 def test_free_slip_flipping_the_tangential_component_is_caught(monkeypatch):

@@ -1,6 +1,8 @@
 """Pins of the oracle's wall reflections (no-slip half-way bounce-back and
 free-slip specular reflection on the y / z faces; Section 3.2 names no-slip
 tank walls and a free-slip top)."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -131,3 +133,29 @@ def test_x_wall_rules():
     with pytest.raises(ValueError):
         NestedSolver("d3q27", (3, 2, 2), periodic_x=False, refine=[r], walls=16)
     NestedSolver("d3q27", (3, 2, 2), periodic_x=False, refine=[r], walls=32)
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("walls,slip", [(3, 0), (15, 12)])
+def test_shear_mode_between_no_slip_walls_decays_at_the_channel_rate(model, walls, slip):
+    """u_x = A sin(pi (y + 1/2) / NY) between no-slip y walls (half a cell
+    outside the boundary cells; free-slip z walls in the second case, which
+    leave the mode alone) decays at nu (pi / NY)^2 within 0.5 %."""
+    tau = 0.8
+    s = NestedSolver(model, (1, 2, 1), periodic_x=True, omega=1 / tau, cs=0.0, walls=walls, slip=slip)
+    lv = s.levels[0]
+    y = torch.arange(lv.NY, dtype=DTYPE) + 0.5
+    mode = torch.sin(math.pi * y / lv.NY)
+    u = torch.zeros(3, lv.NZ, lv.NY, lv.NX, dtype=DTYPE)
+    u[0] = 1e-3 * mode[None, :, None]
+    s.init_equilibrium(0, None, u)
+
+    def amplitude():
+        _, uu = s.macroscopic(0)
+        return float((uu[0, 0, :, 0] * mode).sum() / (mode * mode).sum())
+    s.step(20)
+    a0 = amplitude()
+    s.step(200)
+    rate = -math.log(amplitude() / a0) / 200
+    expect = (tau - 0.5) / 3 * (math.pi / lv.NY) ** 2
+    assert abs(rate / expect - 1) <= 0.005, rate / expect - 1
