@@ -159,3 +159,28 @@ def test_paper_tank_all_boundaries_f64(model, walls):
     d, _ = compare_levels(ctx, orc)
     assert d <= 1e-12, d
     lbm.lbm_destroy(ctx)
+
+
+def test_full_size_paper_tank_keeps_rest():
+    """The bench's paper-tank grid at full size (coarse 384x192x192, walls,
+    free-slip top, pressure outlet at rho_out = 1, the nozzle on the fine
+    level) with zero inflow: every boundary maps the rest state to itself, so
+    three coarse steps leave it at rest to FP32 round-off."""
+    lbm = gpu()
+    flags, centre = synth.jet_two_level()
+    flags = [flags[0].copy()]
+    flags[0][:, :, -1] = False
+    ctx = lbm.lbm_create("d3q27", "f32", (48, 24, 24), False, flags, 1.0 / (3 * 8e-5 + 0.5), 0.0,
+                         walls=15, slip=8, outlet=1, nozzle=(centre[0], centre[1], 8.0, 8.0, 48.0))
+    lbm.lbm_set_outlet(ctx, 1.0)
+    lbm.lbm_set_inflow(ctx, centre[0], centre[1], 16.0, 0.0, 0.01, 3)
+    for l in range(2):
+        lbm.lbm_init_equilibrium(ctx, l)
+    lbm.lbm_step(ctx, 3)
+    for l in range(2):
+        rho, u = lbm.lbm_macroscopic(ctx, l)
+        ok = ~np.isnan(rho)
+        assert ok.sum() > 0
+        assert np.abs(rho[ok] - 1).max() <= 1e-6
+        assert np.abs(u[:, ok]).max() <= 1e-7
+    lbm.lbm_destroy(ctx)
