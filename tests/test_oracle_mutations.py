@@ -97,22 +97,33 @@ def test_missing_interface_rescaling_is_caught(monkeypatch):
     assert fails(TN.test_shear_wave_stress_crosses_interfaces, "d3q19")
 
 
-def test_wrong_temporal_interpolation_is_caught(monkeypatch):
+def _weighted_c2f(monkeypatch, w):
+    """Plant F_1 = (1 - w) f~(t) + w f~(t+1) for the second fine substep."""
+    orig = S.NestedSolver._c2f
+
+    def c2f(self, l, s, old, new, oldS, newS):
+        if s == 0:
+            return orig(self, l, 0, old, new, oldS, newS)
+        mix, mixS = (1 - w) * old + w * new, (1 - w) * oldS + w * newS
+        return orig(self, l, 0, mix, mix, mixS, mixS)
+    monkeypatch.setattr(S.NestedSolver, "_c2f", c2f)
+
+
+@pytest.mark.parametrize("w", [0.0, 0.4, 0.6, 1.0])
+def test_wrong_temporal_weight_is_caught(monkeypatch, w):
+    """Old-only (0), new-only (1) and a slightly wrong weight (0.4, 0.6)
+    each break the closed-form phase speed of the drifting wave."""
+    _weighted_c2f(monkeypatch, w)
+    assert fails(TN.test_drifting_wave_crosses_interfaces_at_the_exact_phase_speed, 0.05)
+
+
+def test_new_only_temporal_interpolation_on_both_substeps_is_caught(monkeypatch):
     orig = S.NestedSolver._c2f
 
     def c2f(self, l, s, old, new, oldS, newS):
         return orig(self, l, 0, new, new, newS, newS)   # always the new coarse values
     monkeypatch.setattr(S.NestedSolver, "_c2f", c2f)
-    assert fails(TN.test_shear_wave_across_refined_slab, "d3q19")
-
-
-def test_old_only_temporal_interpolation_is_caught(monkeypatch):
-    orig = S.NestedSolver._c2f
-
-    def c2f(self, l, s, old, new, oldS, newS):
-        return orig(self, l, 0, old, old, oldS, oldS)   # always the old coarse values
-    monkeypatch.setattr(S.NestedSolver, "_c2f", c2f)
-    assert fails(TN.test_shear_wave_across_refined_slab, "d3q19")
+    assert fails(TN.test_drifting_wave_crosses_interfaces_at_the_exact_phase_speed, 0.05)
 
 
 def test_wrong_inflow_velocity_is_caught(monkeypatch):
