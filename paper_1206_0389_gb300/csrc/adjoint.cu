@@ -260,7 +260,7 @@ __device__ __forceinline__ void collide27_adjoint(const T* g, T* lam, T omega, T
 
 // One adjoint step over all blocks of a periodic single level (CTA = block).
 template <class T, int TPB>
-__global__ void __launch_bounds__(TPB) k_adjoint(const AdjointArgs a) {
+__global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 4 : 1) k_adjoint(const AdjointArgs a) {
   constexpr int Q = 27;
   constexpr int QS = Q * kCells;
   const T* __restrict__ fsrc = reinterpret_cast<const T*>(a.f_t);
@@ -271,17 +271,22 @@ __global__ void __launch_bounds__(TPB) k_adjoint(const AdjointArgs a) {
   for (int b = blockIdx.x; b < a.nblocks; b += gridDim.x) {
     const int bx = b % a.BX, by = (b / a.BX) % a.BY, bz = b / (a.BX * a.BY);
     const int BXY = a.BX * a.BY;
+    // x / y block offsets fit an int (the planner keeps BX * BY * 27 * 512
+    // below 2^31); a periodic z wrap moves by up to nblocks * 27 * 512
+    // elements, so the z neighbours enter through 64-bit base indices
     const int dxm = bx == 0 ? a.BX - 1 : -1, dxp = bx == a.BX - 1 ? -(a.BX - 1) : 1;
     const int dym = by == 0 ? a.BX * (a.BY - 1) : -a.BX, dyp = by == a.BY - 1 ? -a.BX * (a.BY - 1) : a.BX;
-    const int dzm = bz == 0 ? BXY * (a.BZ - 1) : -BXY, dzp = bz == a.BZ - 1 ? -BXY * (a.BZ - 1) : BXY;
+    const int64_t dzm = bz == 0 ? int64_t(BXY) * (a.BZ - 1) : -int64_t(BXY);
+    const int64_t dzp = bz == a.BZ - 1 ? -int64_t(BXY) * (a.BZ - 1) : int64_t(BXY);
 #pragma unroll 1
     for (int c = threadIdx.x; c < kCells; c += TPB) {
       const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
       const int Xm = (x == 0) ? dxm * QS + 8 : 0, Xp = (x == 7) ? dxp * QS - 8 : 0;
       const int Ym = (y == 0) ? dym * QS + 64 : 0, Yp = (y == 7) ? dyp * QS - 64 : 0;
-      const int Zm = (z == 0) ? dzm * QS + 512 : 0, Zp = (z == 7) ? dzp * QS - 512 : 0;
       const int64_t own = int64_t(b) * QS + c;
-      // element offset of population i's pull source (= its adjoint target)
+      const int64_t B1 = z == 0 ? own + dzm * QS + 512 : own;   // base of e_z = +1 pulls
+      const int64_t Bm = z == 7 ? own + dzp * QS - 512 : own;   // base of e_z = -1 pulls
+      // element index of population i's pull source (= its adjoint target)
       auto pull = [&](auto i) {
         constexpr int ex = D3Q27::ex(i), ey = D3Q27::ey(i), ez = D3Q27::ez(i);
         int o = int(i) * kCells - (ex + 8 * ey + 64 * ez);
@@ -289,13 +294,11 @@ __global__ void __launch_bounds__(TPB) k_adjoint(const AdjointArgs a) {
         if constexpr (ex == -1) o += Xp;
         if constexpr (ey == 1) o += Ym;
         if constexpr (ey == -1) o += Yp;
-        if constexpr (ez == 1) o += Zm;
-        if constexpr (ez == -1) o += Zp;
-        return o;
+        return (ez == 1 ? B1 : ez == -1 ? Bm : own) + o;
       };
       T g[Q], lam[Q];
       static_for<Q>([&](auto i) {
-        g[i] = fsrc[own + pull(i)];
+        g[i] = fsrc[pull(i)];
         lam[i] = lin[own + int(i) * kCells];
       });
       const int64_t j = int64_t(b) * kCells + c;
@@ -308,7 +311,7 @@ __global__ void __launch_bounds__(TPB) k_adjoint(const AdjointArgs a) {
       }
       T Fbx = T(0), Fby = T(0), Fbz = T(0);
       collide27_adjoint<T>(g, lam, T(a.omega), Fx, Fy, Fz, Fbx, Fby, Fbz);
-      static_for<Q>([&](auto i) { lout[own + pull(i)] = lam[i]; });
+      static_for<Q>([&](auto i) { lout[pull(i)] = lam[i]; });
       gF[j] += Fbx;
       gF[ncell + j] += Fby;
       gF[2 * ncell + j] += Fbz;

@@ -260,7 +260,12 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
     lp.wrap[1] = lp.BY == d.nby;
     lp.wrap[2] = lp.BZ == d.nbz;
     const int64_t nb = lp.nblocks();
-    if (nb * 512 * P.Q >= (int64_t(1) << 46)) return "level box too large";
+    if (nb * 512 * P.Q >= (int64_t(1) << 46) || nb >= (int64_t(1) << 31)) return "level box too large";
+    // the streaming kernels form x / y neighbour offsets in 32 bits (z
+    // neighbours go through 64-bit bases): one z layer of blocks must stay
+    // below 2^31 stored values
+    if (int64_t(lp.BX) * lp.BY * 512 * P.Q >= (int64_t(1) << 31))
+      return "level box cross-section too large: BX * BY * Q * 512 must be below 2^31";
     lp.kind.assign(nb * 512, K_NONE);
 
     auto box_of = [&](int bx, int by, int bz) -> int32_t {  // domain coords (wrapped)

@@ -67,13 +67,18 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
     const WorkItem w = a.items[it];
     const LevelPtrs& L = a.lv[w.level];
     const int BX = L.BX, BXY = L.BX * L.BY;
-    // block deltas towards -x, +x, -y, +y, -z, +z (periodic wrap on box faces)
+    // block deltas towards -x, +x, -y, +y (periodic wrap on box faces); the
+    // planner keeps BX * BY * Q * 512 below 2^31, so x and y offsets fit an
+    // int.  A wrap across z moves by up to nblocks * Q * 512 elements, past
+    // the int range on large boxes: the blocks below and above are reached
+    // through 64-bit base pointers instead (zlo: the source of e_z = +1 pulls
+    // of the cells z == 0, zhi: of e_z = -1 pulls of the cells z == 7).
     const int dxm = (w.edges & 1) ? (L.BX - 1) : -1;
     const int dxp = (w.edges & 2) ? -(L.BX - 1) : 1;
     const int dym = (w.edges & 4) ? BX * (L.BY - 1) : -BX;
     const int dyp = (w.edges & 8) ? -BX * (L.BY - 1) : BX;
-    const int dzm = (w.edges & 16) ? BXY * (L.BZ - 1) : -BXY;
-    const int dzp = (w.edges & 32) ? -BXY * (L.BZ - 1) : BXY;
+    const int64_t dzm = (w.edges & 16) ? int64_t(BXY) * (L.BZ - 1) : -int64_t(BXY);
+    const int64_t dzp = (w.edges & 32) ? -int64_t(BXY) * (L.BZ - 1) : int64_t(BXY);
     // wall faces this block touches (bit 0/1 low/high y, 2/3 low/high z):
     // the level-0 box spans the domain in y and z, so its wrapping faces
     // are the walls; the x faces come from edges bits 7 (x = 0) and 6 (the
@@ -84,20 +89,29 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
     const T tau0 = T(L.tau0);
     const S* __restrict__ src = reinterpret_cast<const S*>(L.src) + int64_t(w.block) * QS;
     S* __restrict__ dst = reinterpret_cast<S*>(L.dst) + int64_t(w.block) * QS;
-    // source of population i for cell c: own block + i*512 + c - (e_x + 8 e_y
-    // + 64 e_z) + the block offsets of the faces the pull crosses
-    auto offsets = [&](int c, int& Xm, int& Xp, int& Ym, int& Yp, int& Zm, int& Zp) {
-      const int x = c & 7, y = (c >> 3) & 7, z = c >> 6;
+    const S* zlo = src + (dzm * QS + 512);
+    const S* zhi = src + (dzp * QS - 512);
+    // source of population i for cell c: base(e_z) + c + i*512 - (e_x + 8 e_y
+    // + 64 e_z) + the x / y block offsets of the faces the pull crosses, with
+    // base(0) = src, base(+1) = zlo for z == 0 (else src), base(-1) = zhi for
+    // z == 7 (else src)
+    auto offsets = [&](int c, int& Xm, int& Xp, int& Ym, int& Yp) {
+      const int x = c & 7, y = (c >> 3) & 7;
       Xm = (x == 0) ? dxm * QS + 8 : 0;
       Xp = (x == 7) ? ((w.edges & 64) ? -1 : dxp * QS - 8) : 0;
       Ym = (y == 0) ? dym * QS + 64 : 0;
       Yp = (y == 7) ? dyp * QS - 64 : 0;
-      Zm = (z == 0) ? dzm * QS + 512 : 0;
-      Zp = (z == 7) ? dzp * QS - 512 : 0;
+    };
+    auto zbase = [&](int c, const S*& b1, const S*& bm) {
+      const int z = c >> 6;
+      b1 = (z == 0 ? zlo : src) + c;
+      bm = (z == 7 ? zhi : src) + c;
     };
     auto pull = [&](int c, auto&& load) {
-      int Xm, Xp, Ym, Yp, Zm, Zp;
-      offsets(c, Xm, Xp, Ym, Yp, Zm, Zp);
+      int Xm, Xp, Ym, Yp;
+      offsets(c, Xm, Xp, Ym, Yp);
+      const S *b1, *bm;
+      zbase(c, b1, bm);
       const S* p = src + c;
       static_for<Q>([&](auto i) {
         constexpr int ex = Lattice<Q>::ex(i), ey = Lattice<Q>::ey(i), ez = Lattice<Q>::ez(i);
@@ -107,9 +121,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
         if constexpr (ex == -1) o += Xp;
         if constexpr (ey == 1) o += Ym;
         if constexpr (ey == -1) o += Yp;
-        if constexpr (ez == 1) o += Zm;
-        if constexpr (ez == -1) o += Zp;
-        load(i, p + o + k);
+        if constexpr (ez == 1) load(i, b1 + o + k);
+        else if constexpr (ez == -1) load(i, bm + o + k);
+        else load(i, p + o + k);
       });
     };
     auto active = [&](int c) {
@@ -125,8 +139,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
       const bool zl = (wf & 4) && z == 0, zh = (wf & 8) && z == 7;
       const bool xl = (wf & 16) && x == 0, xh = (wf & 32) && x == 7;
       if (!(yl || yh || zl || zh || xl || xh)) return;
-      int Xm, Xp, Ym, Yp, Zm, Zp;
-      offsets(c, Xm, Xp, Ym, Yp, Zm, Zp);
+      int Xm, Xp, Ym, Yp;
+      offsets(c, Xm, Xp, Ym, Yp);
+      const S *b1, *bm;
+      zbase(c, b1, bm);
       const S* p = src + c;
       static_for<Q>([&](auto i) {
         constexpr int ex = Lattice<Q>::ex(i), ey = Lattice<Q>::ey(i), ez = Lattice<Q>::ez(i);
@@ -138,18 +154,19 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
             const bool sy = a.slip & (ey == 1 ? 1 : 2), sz = a.slip & (ez == 1 ? 4 : 8);
             const int X = ex == 1 ? Xm : ex == -1 ? Xp : 0;
             const int Y = ey == 1 ? Ym : ey == -1 ? Yp : 0;
-            const int Z = ez == 1 ? Zm : ez == -1 ? Zp : 0;
             constexpr int ib = Lattice<Q>::index(-ex, -ey, -ez);
             constexpr int iy = Lattice<Q>::index(ex, -ey, ez);
             constexpr int iz = Lattice<Q>::index(ex, ey, -ez);
             constexpr int iyz = Lattice<Q>::index(ex, -ey, -ez);
-            int o;
-            if (cx || (cy && !sy) || (cz && !sz)) o = ib * kCells;
-            else if (cy && cz) o = iyz * kCells - ex + X;
-            else if (cy) o = iy * kCells - (ex + 64 * ez) + X + Z;
-            else o = iz * kCells - (ex + 8 * ey) + X + Y;
-            if constexpr (kScaled) g[i] = __half2float(__ldg(p + o));
-            else g[i] = St::template get<Q, i>(p + o);
+            // the reflected source: the cell itself (bounce-back), or the
+            // pull along the axes not crossed (z pulls from the z base)
+            const S* q;
+            if (cx || (cy && !sy) || (cz && !sz)) q = p + ib * kCells;
+            else if (cy && cz) q = p + (iyz * kCells - ex + X);
+            else if (cy) q = (ez == 1 ? b1 : ez == -1 ? bm : p) + (iy * kCells - (ex + 64 * ez) + X);
+            else q = p + (iz * kCells - (ex + 8 * ey) + X + Y);
+            if constexpr (kScaled) g[i] = __half2float(__ldg(q));
+            else g[i] = St::template get<Q, i>(q);
           }
         }
       });

@@ -83,6 +83,23 @@ def test_jet_plan_sizes():
     assert info.active_updates_per_coarse_step == 25_952_256
 
 
+@pytest.mark.parametrize("model,Q", [("d3q27", 27), ("d3q19", 19)])
+def test_plan_rejects_a_cross_section_just_past_the_32_bit_offset_limit(model, Q):
+    """The stream-collide kernels form x / y neighbour offsets in 32 bits
+    (one z layer of blocks below 2^31 stored values; z neighbours use 64-bit
+    bases): the planner accepts the largest such layer and refuses the next."""
+    from paper_1206_0389_gb300 import lbm
+    limit = (1 << 31) // (512 * Q)          # blocks per z layer that still fit
+    nbx = 512
+    ok_y, bad_y = limit // nbx, limit // nbx + 1
+    assert nbx * ok_y * 512 * Q < 1 << 31 <= nbx * bad_y * 512 * Q
+    info = lbm.lbm_plan((nbx, ok_y, 1), True, [], model, "f16")
+    assert info.blocks[0] == nbx * ok_y
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_plan((nbx, bad_y, 1), True, [], model, "f16")
+    assert e.value.status == lbm.LBM_ERR_ARG
+
+
 def test_plan_rejects_bad_grids():
     r0 = np.zeros((2, 2, 3), dtype=bool)
     r0[:, :, 0:2] = True
