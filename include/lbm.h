@@ -282,18 +282,32 @@ int lbm_set_step(lbm_ctx* ctx, int64_t step);
 
 /* Discrete adjoint of the forced D3Q27 FCLB update (single periodic level,
  * F32 or F64 storage; the paper has no adjoint: this serves gradient-based
- * studies of the same update).  Two phases with sqrt(T)-style checkpointing:
- * lbm_adjoint_forward advances T steps from the current state (with the force
- * of lbm_set_force), keeping a copy of the state every checkpoint_every steps;
- * the final state is then the context's state.  lbm_adjoint_backward takes
- * dL/df_T (host, float64, dense [27][NZ][NY][NX], w.r.t. the distributions
- * after step T) and returns dL/dF (host, float64, dense [3][NZ][NY][NX]) of a
- * force held constant over the T steps.  Each segment of checkpoint_every
- * steps is recomputed from its checkpoint, then swept backwards with the
- * adjoint stream-collide kernel.  Device memory: (T/checkpoint_every +
- * checkpoint_every + 2) states plus the dL/dF accumulator.  LBM_ERR_STATE for
- * other grids or models, or backward without a forward. */
+ * studies of the same update).  Two phases: lbm_adjoint_forward advances T
+ * steps from the current state (with the force of lbm_set_force) and records
+ * what the backward sweep needs; the final state is then the context's state.
+ * lbm_adjoint_backward takes dL/df_T (host, float64, dense [27][NZ][NY][NX],
+ * w.r.t. the distributions after step T) and returns dL/dF (host, float64,
+ * dense [3][NZ][NY][NX]) of a force held constant over the T steps, sweeping
+ * the steps backwards with the adjoint stream-collide kernel.
+ *   checkpoint_every = 1: every step's input state is kept (the forward
+ *     writes each step straight into its slot); the backward sweep needs no
+ *     recomputation.  Device memory: T + 2 states plus dL/dF.
+ *   checkpoint_every = k > 1: sqrt(T)-style checkpointing; a copy of the
+ *     state every k steps, each segment recomputed from its checkpoint
+ *     before its backward sweep.  Device memory: (T/k + k + 2) states.
+ *   checkpoint_every = 0: the library chooses 1 when T + 2 states fit in
+ *     half of the free device memory (counting adjoint buffers it already
+ *     holds), else ceil(sqrt(T)).
+ * lbm_adjoint_forward returns LBM_ERR_OOM, with every adjoint buffer freed,
+ * when an allocation fails.  lbm_set_force and a failed forward discard the
+ * recorded forward: lbm_adjoint_backward then returns LBM_ERR_STATE, as it
+ * does for other grids or models or without a forward. */
 int lbm_adjoint_forward(lbm_ctx* ctx, int T, int checkpoint_every);
+/* Number of completed lbm_adjoint_forward calls on ctx while the last one's
+ * record is valid, else 0; a caller that keeps several forwards apart (an
+ * autograd graph) compares it before lbm_adjoint_backward.  checkpoint_every
+ * (may be NULL) receives the spacing that forward used (0 if none). */
+int lbm_adjoint_generation(const lbm_ctx* ctx, uint64_t* generation, int* checkpoint_every);
 int lbm_adjoint_backward(lbm_ctx* ctx, const double* dLdf_T, double* dLdF);
 
 /* Kernel timing: when enabled, lbm_step launches kernels directly (no graph)
@@ -332,9 +346,11 @@ int lbm_get_tuning(const lbm_ctx* ctx, int* threads, int* min_ctas_per_sm, int* 
  * library keeps until exit.  Returns LBM_ERR_ARG for a bad model/storage, a
  * NULL pointer, or nblocks outside 1..LBM_NOALLOC_MAX_BLOCKS (the static
  * array holds one partial sum per block); LBM_ERR_CUDA on a launch error.
- * All calls share the array: calls that overlap on the same GPU race.  The
- * first call on a device looks up the array's address; make it before any
- * stream capture. */
+ * All calls share the array: calls that overlap on the same GPU race.  A
+ * call whose stream is not capturing looks up the array's device address
+ * and remembers it per device; a call under stream capture uses the
+ * remembered address (LBM_ERR_CUDA if there is none), so make the first call
+ * on a device, and the first after a cudaDeviceReset, outside capture. */
 #define LBM_NOALLOC_MAX_BLOCKS 65536
 int lbm_mass_momentum_noalloc(int model, int storage, const void* f, int64_t nblocks, double* out,
                               void* cuda_stream);

@@ -96,6 +96,8 @@ struct lbm_ctx {
   // adjoint: checkpoints every `every` steps, segment buffers, lambda, dL/dF
   int adj_T = 0, adj_every = 0;
   bool adj_ready = false;
+  uint64_t adj_gen = 0;  // completed lbm_adjoint_forward calls
+  long long step_dev = 0;  // host source of a device step-counter update
   std::vector<void*> adj_ck, adj_seg;
   void* adj_lam[2] = {nullptr, nullptr};
   void* adj_gF = nullptr;
@@ -131,6 +133,20 @@ cudaError_t upload(T** dst, const std::vector<T>& v) {
   return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+// frees the adjoint buffers and forgets the recorded forward
+void release_adjoint(lbm_ctx* c) {
+  for (void* p : c->adj_ck) cudaFree(p);
+  for (void* p : c->adj_seg) cudaFree(p);
+  cudaFree(c->adj_lam[0]);
+  cudaFree(c->adj_lam[1]);
+  cudaFree(c->adj_gF);
+  c->adj_ck.clear();
+  c->adj_seg.clear();
+  c->adj_lam[0] = c->adj_lam[1] = c->adj_gF = nullptr;
+  c->adj_state_bytes = 0;
+  c->adj_ready = false;
+}
+
 void free_all(lbm_ctx* c) {
   for (int p = 0; p < 2; ++p)
     if (c->graph[p]) cudaGraphExecDestroy(c->graph[p]);
@@ -158,11 +174,7 @@ void free_all(lbm_ctx* c) {
   cudaFree(c->d_out);
   cudaFree(c->d_flag);
   cudaFree(c->stage);
-  for (void* p : c->adj_ck) cudaFree(p);
-  for (void* p : c->adj_seg) cudaFree(p);
-  cudaFree(c->adj_lam[0]);
-  cudaFree(c->adj_lam[1]);
-  cudaFree(c->adj_gF);
+  release_adjoint(c);
   for (cudaEvent_t e : c->fork_join) cudaEventDestroy(e);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -799,6 +811,8 @@ int lbm_init_equilibrium(lbm_ctx* ctx, int level, const double* rho, const doubl
 
 int lbm_set_force(lbm_ctx* ctx, const double* F) {
   if (!ctx) return LBM_ERR_ARG;
+  // the backward sweep reads the force: a recorded forward no longer matches
+  ctx->adj_ready = false;
   if (F == nullptr) {
     ctx->has_force = false;
     ctx->graphs_valid = false;
@@ -1235,57 +1249,102 @@ int lbm_adjoint_forward(lbm_ctx* ctx, int T, int checkpoint_every) {
   if (ctx->plan.walls || ctx->plan.nozzle_level >= 0)
     return fail(ctx, LBM_ERR_STATE, "the adjoint is defined without walls or a nozzle");
   if (ctx->storage == LBM_F16) return fail(ctx, LBM_ERR_STATE, "the adjoint needs F32 or F64 storage");
-  if (T < 1 || checkpoint_every < 1 || checkpoint_every > T)
-    return fail(ctx, LBM_ERR_ARG, "need T >= 1 and 1 <= checkpoint_every <= T");
+  if (T < 1 || checkpoint_every < 0 || checkpoint_every > T)
+    return fail(ctx, LBM_ERR_ARG, "need T >= 1 and 0 <= checkpoint_every <= T");
   const LevelPlan& lp = ctx->plan.lv[0];
   const size_t sb = size_t(lp.nblocks()) * 512 * 27 * storage_bytes(ctx->storage);
-  const int nck = (T + checkpoint_every - 1) / checkpoint_every;
-  if (ctx->adj_state_bytes != sb || int(ctx->adj_ck.size()) < nck || int(ctx->adj_seg.size()) < checkpoint_every) {
+  const size_t gb = size_t(lp.nblocks()) * 512 * 3 * real_bytes(ctx->storage);
+  int every = checkpoint_every;
+  if (every == 0) {
+    // keep every state when T of them (plus the two adjoint buffers) fit in
+    // half of the free device memory, counting what the adjoint already holds
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    size_t held = ctx->adj_gF ? gb : 0;
+    for (void* p : ctx->adj_ck) held += p ? ctx->adj_state_bytes : 0;
+    for (void* p : ctx->adj_seg) held += p ? ctx->adj_state_bytes : 0;
+    for (void* p : ctx->adj_lam) held += p ? ctx->adj_state_bytes : 0;
+    every = (double(T) + 2.0) * double(sb) + double(gb) <= 0.5 * double(fr + held)
+                ? 1
+                : std::max(1, int(std::ceil(std::sqrt(double(T)))));
+  }
+  const int nck = (T + every - 1) / every;
+  if (ctx->adj_state_bytes != sb || int(ctx->adj_ck.size()) < nck || int(ctx->adj_seg.size()) < every) {
     CK(cudaStreamSynchronize(ctx->stream));
-    for (void* p : ctx->adj_ck) cudaFree(p);
-    for (void* p : ctx->adj_seg) cudaFree(p);
-    cudaFree(ctx->adj_lam[0]);
-    cudaFree(ctx->adj_lam[1]);
-    cudaFree(ctx->adj_gF);
-    ctx->adj_ck.clear();
-    ctx->adj_seg.clear();
-    ctx->adj_lam[0] = ctx->adj_lam[1] = ctx->adj_gF = nullptr;
-    ctx->adj_state_bytes = sb;
+    release_adjoint(ctx);
+    // LBM_INJECT_ADJOINT_OOM=k makes the k-th buffer allocation below fail on
+    // the host, as cudaMalloc would when the device is full (tests of the
+    // failure path; no device fault is involved)
+    int inject = 0;
+    if (const char* e = std::getenv("LBM_INJECT_ADJOINT_OOM")) inject = std::atoi(e);
+    int grabs = 0;
     auto grab = [&](void** p, size_t n) -> int {
-      cudaError_t e = cudaMalloc(p, n);
-      if (e != cudaSuccess) return fail(ctx, LBM_ERR_OOM, std::string("adjoint buffers: ") + cudaGetErrorString(e));
+      cudaError_t e = (inject > 0 && ++grabs == inject) ? cudaErrorMemoryAllocation : cudaMalloc(p, n);
+      if (e != cudaSuccess) {
+        // nothing half-allocated stays behind: the next call starts afresh
+        release_adjoint(ctx);
+        return fail(ctx, LBM_ERR_OOM, std::string("adjoint buffers: ") + cudaGetErrorString(e));
+      }
       return LBM_OK;
     };
     ctx->adj_ck.assign(nck, nullptr);
-    ctx->adj_seg.assign(checkpoint_every, nullptr);
-    for (auto& p : ctx->adj_ck)
-      if (int rc = grab(&p, sb)) return rc;
+    ctx->adj_seg.assign(every, nullptr);
+    for (size_t k = 0; k < ctx->adj_ck.size(); ++k)
+      if (int rc = grab(&ctx->adj_ck[k], sb)) return rc;
     for (size_t k = 1; k < ctx->adj_seg.size(); ++k)
       if (int rc = grab(&ctx->adj_seg[k], sb)) return rc;
     for (int k = 0; k < 2; ++k)
       if (int rc = grab(&ctx->adj_lam[k], sb)) return rc;
-    if (int rc = grab(&ctx->adj_gF, size_t(lp.nblocks()) * 512 * 3 * real_bytes(ctx->storage))) return rc;
+    if (int rc = grab(&ctx->adj_gF, gb)) return rc;
+    ctx->adj_state_bytes = sb;
   }
   if (ctx->need_restrict) {
     int rc = restrict_all(ctx);
     if (rc) return rc;
   }
-  if (!ctx->graphs_valid) {
-    int rc = build_graphs(ctx);
-    if (rc) return rc;
-  }
   ctx->adj_ready = false;
-  for (int t = 0; t < T; ++t) {
-    if (t % checkpoint_every == 0)
-      CK(cudaMemcpyAsync(ctx->adj_ck[t / checkpoint_every], ctx->dl[0].f[ctx->parity0], sb,
-                         cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaGraphLaunch(ctx->graph[ctx->parity0], ctx->stream));
+  if (every == 1) {
+    // every state kept: the update writes step t's input straight into its
+    // slot (no copies); the last step writes the context's other buffer
+    std::vector<Op> ops = build_schedule(ctx, ctx->parity0);
+    UpdateArgs ua{};
+    for (const Op& op : ops)
+      if (op.kind == Op::UPDATE) ua = op.ua;
+    CK(cudaMemcpyAsync(ctx->adj_ck[0], ctx->dl[0].f[ctx->parity0], sb, cudaMemcpyDeviceToDevice, ctx->stream));
+    for (int t = 0; t < T; ++t) {
+      ua.lv[0].src = ctx->adj_ck[t];
+      ua.lv[0].dst = t + 1 < T ? ctx->adj_ck[t + 1] : ctx->dl[0].f[1 - ctx->parity0];
+      CK(launch_update(ctx->model, ctx->storage, ua, ctx->threads, ctx->minb, ctx->ctas, ctx->stream));
+    }
     ctx->parity0 ^= 1;
-    ctx->step++;
+    ctx->step += T;
+    ctx->step_dev = ctx->step;
+    CK(cudaMemcpyAsync(ctx->d_step, &ctx->step_dev, sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    if (!ctx->graphs_valid) {
+      int rc = build_graphs(ctx);
+      if (rc) return rc;
+    }
+    for (int t = 0; t < T; ++t) {
+      if (t % every == 0)
+        CK(cudaMemcpyAsync(ctx->adj_ck[t / every], ctx->dl[0].f[ctx->parity0], sb, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+      CK(cudaGraphLaunch(ctx->graph[ctx->parity0], ctx->stream));
+      ctx->parity0 ^= 1;
+      ctx->step++;
+    }
   }
   ctx->adj_T = T;
-  ctx->adj_every = checkpoint_every;
+  ctx->adj_every = every;
   ctx->adj_ready = true;
+  ctx->adj_gen++;
+  return LBM_OK;
+}
+
+int lbm_adjoint_generation(const lbm_ctx* ctx, uint64_t* generation, int* checkpoint_every) {
+  if (!ctx || !generation) return LBM_ERR_ARG;
+  *generation = ctx->adj_ready ? ctx->adj_gen : 0;
+  if (checkpoint_every) *checkpoint_every = ctx->adj_ready ? ctx->adj_every : 0;
   return LBM_OK;
 }
 

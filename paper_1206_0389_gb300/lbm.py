@@ -24,7 +24,7 @@ EXPORTED = ["lbm_plan", "lbm_create", "lbm_create_error", "lbm_set_inflow", "lbm
             "lbm_set_force", "lbm_step", "lbm_sync", "lbm_macroscopic", "lbm_mass_momentum",
             "lbm_get_state", "lbm_set_state", "lbm_get_cells", "lbm_get_step", "lbm_set_step",
             "lbm_set_profiling", "lbm_get_profile", "lbm_get_tuning", "lbm_last_error", "lbm_destroy",
-            "lbm_mass_momentum_noalloc", "lbm_adjoint_forward", "lbm_adjoint_backward",
+            "lbm_mass_momentum_noalloc", "lbm_adjoint_forward", "lbm_adjoint_backward", "lbm_adjoint_generation",
             "lbm_get_strain", "lbm_set_strain", "lbm_raw_state_bytes", "lbm_get_raw_state",
             "lbm_set_raw_state", "lbm_stats_reset", "lbm_stats_accumulate", "lbm_stats_get",
             "lbm_stats_radial", "lbm_jet_fit"]
@@ -101,6 +101,7 @@ def load():
         "lbm_mass_momentum_noalloc": (c_int, [c_int, c_int, c_void_p, c_int64, c_void_p, c_void_p]),
         "lbm_adjoint_forward": (c_int, [c_void_p, c_int, c_int]),
         "lbm_adjoint_backward": (c_int, [c_void_p, D, D]),
+        "lbm_adjoint_generation": (c_int, [c_void_p, P(c_uint64), P(c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -340,6 +341,13 @@ def lbm_get_profile(ctx):
 
 def lbm_adjoint_forward(ctx, T, checkpoint_every):
     _check(ctx, load().lbm_adjoint_forward(ctx.h, int(T), int(checkpoint_every)))
+
+
+def lbm_adjoint_generation(ctx):
+    """(generation, checkpoint_every) of the recorded adjoint forward; (0, 0) if none."""
+    g, e = c_uint64(0), c_int(0)
+    _check(ctx, load().lbm_adjoint_generation(ctx.h, ctypes.byref(g), ctypes.byref(e)))
+    return int(g.value), int(e.value)
 
 
 def lbm_adjoint_backward(ctx, dLdf_T):

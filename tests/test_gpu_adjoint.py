@@ -103,3 +103,98 @@ def test_adjoint_rejects_unsupported_contexts():
         lbm.lbm_adjoint_forward(ctx, 4, 5)
     assert e.value.status == lbm.LBM_ERR_ARG
     lbm.lbm_destroy(ctx)
+
+
+def _backward_with(lbm, ctx, f0, F, T, every, lam):
+    lbm.lbm_set_state(ctx, 0, f0)
+    lbm.lbm_set_force(ctx, F)
+    lbm.lbm_adjoint_forward(ctx, T, every)
+    fT = lbm.lbm_get_state(ctx, 0)
+    return fT, lbm.lbm_adjoint_backward(ctx, lam)
+
+
+def test_store_every_state_equals_checkpointing_bit_for_bit():
+    """checkpoint_every = 1 keeps every state (no recomputation), 0 lets the
+    library choose, 3 checkpoints; the recomputed states are the same
+    kernel's outputs, so final states and gradients agree bit for bit."""
+    from paper_1206_0389_gb300 import lbm
+    N, T = 16, 7
+    f0 = initial_state(N, 11)
+    F = synth.random_force((N, N, N), 11, sigma=1e-4)
+    lam = np.random.default_rng(5).standard_normal((27, N, N, N)) * 1e-3
+    ctx = lbm.lbm_create("d3q27", "f32", (2, 2, 2), True, [], 1.0 / 0.53, 0.0)
+    fT1, g1 = _backward_with(lbm, ctx, f0, F, T, 1, lam)
+    assert lbm.lbm_adjoint_generation(ctx)[1] == 1
+    fT3, g3 = _backward_with(lbm, ctx, f0, F, T, 3, lam)
+    fT0, g0 = _backward_with(lbm, ctx, f0, F, T, 0, lam)
+    assert lbm.lbm_adjoint_generation(ctx)[1] == 1   # a 16^3 grid fits: every state kept
+    assert np.array_equal(fT1, fT3) and np.array_equal(fT1, fT0)
+    assert np.array_equal(g1, g3) and np.array_equal(g1, g0)
+    # the plain stepping path reaches the same final state
+    lbm.lbm_set_state(ctx, 0, f0)
+    lbm.lbm_set_force(ctx, F)
+    lbm.lbm_step(ctx, T)
+    assert np.array_equal(lbm.lbm_get_state(ctx, 0), fT1)
+    lbm.lbm_destroy(ctx)
+
+
+def test_failed_adjoint_allocation_frees_everything_and_retry_works(monkeypatch):
+    """A host-side injected allocation failure (the k-th adjoint buffer) makes
+    the forward return LBM_ERR_OOM and discard the record; the retry
+    allocates everything again and gives the gradient of a clean context."""
+    from paper_1206_0389_gb300 import lbm
+    N, T = 16, 6
+    f0 = initial_state(N, 12)
+    F = synth.random_force((N, N, N), 12, sigma=1e-4)
+    lam = np.random.default_rng(6).standard_normal((27, N, N, N)) * 1e-3
+    ctx = lbm.lbm_create("d3q27", "f32", (2, 2, 2), True, [], 1.0 / 0.53, 0.0)
+    _, gref = _backward_with(lbm, ctx, f0, F, T, 2, lam)
+    # a longer horizon needs more checkpoints: the buffers are allocated anew
+    for k in (1, 7, 9):          # a checkpoint, a segment buffer, a lambda buffer
+        lbm.lbm_set_state(ctx, 0, f0)
+        lbm.lbm_set_force(ctx, F)
+        monkeypatch.setenv("LBM_INJECT_ADJOINT_OOM", str(k))
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_adjoint_forward(ctx, 2 * T, 2)
+        assert e.value.status == lbm.LBM_ERR_OOM
+        monkeypatch.delenv("LBM_INJECT_ADJOINT_OOM")
+        assert lbm.lbm_adjoint_generation(ctx) == (0, 0)
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_adjoint_backward(ctx, lam)
+        assert e.value.status == lbm.LBM_ERR_STATE
+        _, g = _backward_with(lbm, ctx, f0, F, T, 2, lam)
+        assert np.array_equal(g, gref)
+    lbm.lbm_destroy(ctx)
+
+
+def test_second_forward_or_new_force_invalidates_the_first_graph_node():
+    from paper_1206_0389_gb300 import lbm
+    from paper_1206_0389_gb300.autograd import forced_fclb
+    N, T, omega = 16, 4, 1.0 / 0.53
+    f0 = initial_state(N, 13)
+    F = synth.random_force((N, N, N), 13, sigma=1e-4)
+    region = (4, 12, 4, 12, 4, 12)
+    ctx = lbm.lbm_create("d3q27", "f32", (2, 2, 2), True, [], omega, 0.0)
+    F1 = torch.from_numpy(F).clone().requires_grad_(True)
+    F2 = torch.from_numpy(2 * F).clone().requires_grad_(True)
+    L1 = kinetic_energy_loss(forced_fclb(F1, ctx, f0, T, 2), F1, region)
+    L2 = kinetic_energy_loss(forced_fclb(F2, ctx, f0, T, 2), F2, region)
+    with pytest.raises(RuntimeError, match="another adjoint forward"):
+        L1.backward()
+    L2.backward()                  # the latest forward's node still works
+    g2 = F2.grad.numpy().copy()
+    F3 = torch.from_numpy(2 * F).clone().requires_grad_(True)
+    kinetic_energy_loss(forced_fclb(F3, ctx, f0, T, 2), F3, region).backward()
+    assert np.array_equal(g2, F3.grad.numpy())
+    # a new force after the forward discards the record in the library too
+    lbm.lbm_set_state(ctx, 0, f0)
+    lbm.lbm_set_force(ctx, F)
+    lbm.lbm_adjoint_forward(ctx, T, 2)
+    gen = lbm.lbm_adjoint_generation(ctx)[0]
+    assert gen == 4
+    lbm.lbm_set_force(ctx, 2 * F)
+    assert lbm.lbm_adjoint_generation(ctx) == (0, 0)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_adjoint_backward(ctx, np.zeros((27, N, N, N)))
+    assert e.value.status == lbm.LBM_ERR_STATE
+    lbm.lbm_destroy(ctx)
