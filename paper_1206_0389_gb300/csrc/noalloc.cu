@@ -14,9 +14,12 @@
 // loads this library holds it until the process exits.  Every call shares
 // it and it keeps the previous call's contents; each call overwrites the
 // slots it reads, so nothing needs clearing, but two calls that overlap on
-// the same GPU (different streams or threads) race on it.  The first call on
-// a device looks up the array's device address (cudaGetSymbolAddress); make
-// that first call before any stream capture.
+// the same GPU (different streams or threads) race on it.  A call looks up
+// the array's device address on the current device (cudaGetSymbolAddress)
+// whenever its stream is not capturing, and remembers it per device; a call
+// made while its stream is being captured uses the remembered address, so
+// the first call on a device must come before any stream capture (and, after
+// a cudaDeviceReset, the first call again).
 #include <mutex>
 
 #include "collide.cuh"
@@ -32,18 +35,25 @@ constexpr int kMaxDevices = 64;
 double* g_scratch[kMaxDevices] = {nullptr};
 std::mutex g_scratch_mu;
 
-// device address of the static array on the current device (set up once)
-cudaError_t scratch_on_current_device(double** out) {
+// device address of the static array on the current device: looked up
+// again on every call outside stream capture (so a device reset, which
+// moves the array, is picked up), the remembered one under capture
+cudaError_t scratch_on_current_device(cudaStream_t st, double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (g_scratch[dev] == nullptr) {
+  if (cs == cudaStreamCaptureStatusNone) {
     double* p = nullptr;
     e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_partials);
     if (e != cudaSuccess) return e;
     g_scratch[dev] = p;
+  } else if (g_scratch[dev] == nullptr) {
+    return cudaErrorStreamCaptureUnsupported;
   }
   *out = g_scratch[dev];
   return cudaSuccess;
@@ -59,10 +69,12 @@ __global__ void __launch_bounds__(256) k_block_sums(const S* __restrict__ f, dou
   for (int c = threadIdx.x; c < kCells; c += blockDim.x) {
     static_for<Q>([&](auto i) {
       const double g = double(Store<S>::template get<Q, i>(fb + int(i) * kCells + c));
+      // zero velocity components are skipped at compile time (IEEE rules
+      // keep 0.0 * g as a float64 operation otherwise)
       s[0] += g;
-      s[1] += Lattice<Q>::ex(i) * g;
-      s[2] += Lattice<Q>::ey(i) * g;
-      s[3] += Lattice<Q>::ez(i) * g;
+      if constexpr (Lattice<Q>::ex(i) != 0) s[1] += Lattice<Q>::ex(i) > 0 ? g : -g;
+      if constexpr (Lattice<Q>::ey(i) != 0) s[2] += Lattice<Q>::ey(i) > 0 ? g : -g;
+      if constexpr (Lattice<Q>::ez(i) != 0) s[3] += Lattice<Q>::ez(i) > 0 ? g : -g;
     });
   }
   __shared__ double sh[4][8];
@@ -119,9 +131,9 @@ extern "C" int lbm_mass_momentum_noalloc(int model, int storage, const void* f, 
   if (storage != LBM_F64 && storage != LBM_F32 && storage != LBM_F16) return LBM_ERR_ARG;
   if (f == nullptr || out == nullptr || nblocks < 1) return LBM_ERR_ARG;
   if (nblocks > LBM_NOALLOC_MAX_BLOCKS) return LBM_ERR_ARG;  // beyond the static scratch
-  double* part = nullptr;
-  if (scratch_on_current_device(&part) != cudaSuccess) return LBM_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  double* part = nullptr;
+  if (scratch_on_current_device(st, &part) != cudaSuccess) return LBM_ERR_CUDA;
   const int nb = int(nblocks);
   cudaError_t e;
   if (model == LBM_D3Q19_MRT_LES) {

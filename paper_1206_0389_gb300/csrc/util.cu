@@ -154,22 +154,84 @@ __global__ void k_gather(const GatherArgs a) {
 }
 
 // Float64 sums over active cells: (delta rho, j_x, j_y, j_z) times vol.
+//
+// Each thread first sums every population separately over its cells,
+// S_i = sum_cells g_i, and forms delta rho = sum_i S_i and j_a = sum_i e_ia S_i
+// only at the end: Q float64 additions per cell instead of one per non-zero
+// term of the four sums (81 for D3Q27), which matters on a part whose
+// float64 rate is a small fraction of its float32 rate.  For float32 and
+// float16 storage the per-population sums run in float32 pairs (s, e) by
+// Knuth's TwoSum, s + e being the sum of up to kFlush values with the
+// rounding of each addition kept in e, and every kFlush active cells both
+// are added to the float64 sum.  The pair's error over m values is below
+// about m^2 u^2 sum |g| (u = 2^-24), 1e-12 of sum |g| for m = 16, the same
+// order as the bound of plain float64 recursive summation over a thread's
+// values.  The populations are taken in chunks (registers), each chunk
+// one pass over the thread's cells.
+constexpr int kFlush = 16;
+
 template <class M, class S>
-__global__ void k_reduce(const ReduceArgs a) {
+__global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a) {
   constexpr int Q = M::Q;
+  constexpr int P = Q == 19 ? 10 : 9;  // populations per pass
+  constexpr int NP = (Q + P - 1) / P;
+  constexpr bool kPair = !std::is_same<S, double>::value;
   double s[4] = {0, 0, 0, 0};
-  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < a.ncells;
-       t += int64_t(gridDim.x) * blockDim.x) {
-    if (a.kind[t] != K_ACTIVE) continue;
-    const S* f = reinterpret_cast<const S*>(a.f) + (t / kCells) * Q * kCells + t % kCells;
-    static_for<Q>([&](auto i) {
-      const double g = double(Store<S>::template get<Q, i>(f + int(i) * kCells));
-      s[0] += g;
-      s[1] += Lattice<Q>::ex(i) * g;
-      s[2] += Lattice<Q>::ey(i) * g;
-      s[3] += Lattice<Q>::ez(i) * g;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const int64_t t0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  static_for<NP>([&](auto pass) {
+    constexpr int i0 = int(pass) * P;
+    constexpr int n = (Q - i0) < P ? (Q - i0) : P;
+    double D[n];
+    float hs[n], he[n];
+    static_for<n>([&](auto k) {
+      D[k] = 0.0;
+      hs[k] = 0.f;
+      he[k] = 0.f;
     });
-  }
+    int m = 0;
+    for (int64_t t = t0; t < a.ncells; t += stride) {
+      if (a.kind[t] != K_ACTIVE) continue;
+      const S* f = reinterpret_cast<const S*>(a.f) + (t / kCells) * Q * kCells + t % kCells;
+      if constexpr (!kPair) {
+        static_for<n>([&](auto k) { D[k] += f[(i0 + int(k)) * kCells]; });
+      } else {
+        static_for<n>([&](auto k) {
+          // the stored value as the collision sees it (for FP16 the product
+          // h w rounded to float: __fmul_rn keeps the compiler from fusing
+          // it into the addition below, which would sum unrounded products)
+          float g;
+          if constexpr (std::is_same<S, __half>::value)
+            g = __fmul_rn(__half2float(f[(i0 + int(k)) * kCells]), float(Lattice<Q>::w(i0 + int(k))));
+          else
+            g = Store<S>::template get<Q, i0 + int(k)>(f + (i0 + int(k)) * kCells);
+          // TwoSum: x = hs + g exactly equals x + r
+          const float x = hs[k] + g;
+          const float b = x - hs[k];
+          const float r = (hs[k] - (x - b)) + (g - b);
+          hs[k] = x;
+          he[k] += r;
+        });
+        if (++m == kFlush) {
+          static_for<n>([&](auto k) {
+            D[k] += double(hs[k]);
+            D[k] += double(he[k]);
+            hs[k] = 0.f;
+            he[k] = 0.f;
+          });
+          m = 0;
+        }
+      }
+    }
+    static_for<n>([&](auto k) {
+      constexpr int i = i0 + int(k);
+      const double Si = kPair ? (D[k] + double(hs[k])) + double(he[k]) : D[k];
+      s[0] += Si;
+      if constexpr (Lattice<Q>::ex(i) != 0) s[1] += Lattice<Q>::ex(i) > 0 ? Si : -Si;
+      if constexpr (Lattice<Q>::ey(i) != 0) s[2] += Lattice<Q>::ey(i) > 0 ? Si : -Si;
+      if constexpr (Lattice<Q>::ez(i) != 0) s[3] += Lattice<Q>::ez(i) > 0 ? Si : -Si;
+    });
+  });
   __shared__ double sh[4][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll

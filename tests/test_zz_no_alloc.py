@@ -29,19 +29,22 @@ def storage_layout(f_dense, model, storage):
 
 @pytest.mark.parametrize("model,storage", [("d3q27", "f32"), ("d3q19", "f64"), ("d3q27", "f16")])
 def test_noalloc_audit_matches_mass_momentum_twice(model, storage):
+    """Two calls in a row: the second on a smaller grid (fewer blocks, new
+    contents), so slots the first call filled beyond the second call's
+    range stay stale in the shared array and must not leak into its sums."""
     from paper_1206_0389_gb300 import lbm
-    nb = (4, 3, 2)
-    ctx = lbm.lbm_create(model, storage, nb, True, [], 1.6, 0.1)
-    rho, u = synth.taylor_green_3d(32, 0.05, shape=(32, 24, 16))
-    rho = rho + 0.01 * np.sin(np.arange(16))[:, None, None]
-    lbm.lbm_init_equilibrium(ctx, 0, rho, u)
     out = torch.zeros(4, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    for call in range(2):
-        if call == 1:
-            lbm.lbm_step(ctx, 3)          # new contents for the second call
+    for call, (nb, steps) in enumerate((((4, 3, 2), 0), ((2, 2, 1), 3))):
+        shape = tuple(8 * n for n in nb)
+        ctx = lbm.lbm_create(model, storage, nb, True, [], 1.6, 0.1)
+        rho, u = synth.taylor_green_3d(shape[0], 0.05, shape=shape)
+        rho = rho + 0.01 * np.sin(np.arange(shape[2]))[:, None, None]
+        lbm.lbm_init_equilibrium(ctx, 0, rho, u)
+        lbm.lbm_step(ctx, steps)
         ref = lbm.lbm_mass_momentum(ctx)
         host, nblocks = storage_layout(lbm.lbm_get_state(ctx, 0), model, storage)
+        assert nblocks == nb[0] * nb[1] * nb[2]
         dev = torch.from_numpy(host).cuda()
         out.fill_(float("nan"))
         lbm.lbm_mass_momentum_noalloc(model, storage, dev.data_ptr(), nblocks, out.data_ptr(),
@@ -49,7 +52,7 @@ def test_noalloc_audit_matches_mass_momentum_twice(model, storage):
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         assert np.abs(got - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max()), (call, got, ref)
-    lbm.lbm_destroy(ctx)
+        lbm.lbm_destroy(ctx)
 
 
 def test_noalloc_rejects_sizes_beyond_the_static_scratch():
