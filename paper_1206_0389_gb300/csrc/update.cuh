@@ -71,14 +71,16 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
     // planner keeps BX * BY * Q * 512 below 2^31, so x and y offsets fit an
     // int.  A wrap across z moves by up to nblocks * Q * 512 elements, past
     // the int range on large boxes: the blocks below and above are reached
-    // through 64-bit base pointers instead (zlo: the source of e_z = +1 pulls
-    // of the cells z == 0, zhi: of e_z = -1 pulls of the cells z == 7).
+    // through 64-bit base pointers instead (the source bases of e_z = +1 pulls
+    // of the cells z == 0 and of e_z = -1 pulls of the cells z == 7).
     const int dxm = (w.edges & 1) ? (L.BX - 1) : -1;
     const int dxp = (w.edges & 2) ? -(L.BX - 1) : 1;
     const int dym = (w.edges & 4) ? BX * (L.BY - 1) : -BX;
     const int dyp = (w.edges & 8) ? -BX * (L.BY - 1) : BX;
-    const int64_t dzm = (w.edges & 16) ? int64_t(BXY) * (L.BZ - 1) : -int64_t(BXY);
-    const int64_t dzp = (w.edges & 32) ? -int64_t(BXY) * (L.BZ - 1) : int64_t(BXY);
+    // (z block deltas in blocks fit an int: the box holds fewer than 2^31
+    // blocks; the element offset is widened per cell)
+    const int dzm = (w.edges & 16) ? BXY * (L.BZ - 1) : -BXY;
+    const int dzp = (w.edges & 32) ? -BXY * (L.BZ - 1) : BXY;
     // wall faces this block touches (bit 0/1 low/high y, 2/3 low/high z):
     // the level-0 box spans the domain in y and z, so its wrapping faces
     // are the walls; the x faces come from edges bits 7 (x = 0) and 6 (the
@@ -89,12 +91,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
     const T tau0 = T(L.tau0);
     const S* __restrict__ src = reinterpret_cast<const S*>(L.src) + int64_t(w.block) * QS;
     S* __restrict__ dst = reinterpret_cast<S*>(L.dst) + int64_t(w.block) * QS;
-    const S* zlo = src + (dzm * QS + 512);
-    const S* zhi = src + (dzp * QS - 512);
     // source of population i for cell c: base(e_z) + c + i*512 - (e_x + 8 e_y
     // + 64 e_z) + the x / y block offsets of the faces the pull crosses, with
-    // base(0) = src, base(+1) = zlo for z == 0 (else src), base(-1) = zhi for
-    // z == 7 (else src)
+    // base(0) = src, base(+1) = the block below for z == 0 (else src),
+    // base(-1) = the block above for z == 7 (else src)
     auto offsets = [&](int c, int& Xm, int& Xp, int& Ym, int& Yp) {
       const int x = c & 7, y = (c >> 3) & 7;
       Xm = (x == 0) ? dxm * QS + 8 : 0;
@@ -104,8 +104,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
     };
     auto zbase = [&](int c, const S*& b1, const S*& bm) {
       const int z = c >> 6;
-      b1 = (z == 0 ? zlo : src) + c;
-      bm = (z == 7 ? zhi : src) + c;
+      b1 = src + c + (z == 0 ? int64_t(dzm) * QS + 512 : int64_t(0));
+      bm = src + c + (z == 7 ? int64_t(dzp) * QS - 512 : int64_t(0));
     };
     auto pull = [&](int c, auto&& load) {
       int Xm, Xp, Ym, Yp;

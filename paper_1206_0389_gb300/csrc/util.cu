@@ -162,20 +162,23 @@ __global__ void k_gather(const GatherArgs a) {
 // float64 rate is a small fraction of its float32 rate.  For float32 and
 // float16 storage the per-population sums run in float32 pairs (s, e) by
 // Knuth's TwoSum, s + e being the sum of up to kFlush values with the
-// rounding of each addition kept in e, and every kFlush active cells both
-// are added to the float64 sum.  The pair's error over m values is below
+// rounding of each addition kept in e, and every kFlush cells (inactive
+// ones adding zeros) both are added to the float64 sum.  The pair's error over m values is below
 // about m^2 u^2 sum |g| (u = 2^-24), 1e-12 of sum |g| for m = 16, the same
 // order as the bound of plain float64 recursive summation over a thread's
 // values.  The populations are taken in chunks (registers), each chunk
 // one pass over the thread's cells.
 constexpr int kFlush = 16;
+constexpr int kReduceUnroll = 4;  // cells per iteration, their loads issued together
 
 template <class M, class S>
-__global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a) {
+__global__ void __launch_bounds__(256, 2) k_reduce(const ReduceArgs a) {
   constexpr int Q = M::Q;
   constexpr int P = Q == 19 ? 10 : 9;  // populations per pass
   constexpr int NP = (Q + P - 1) / P;
+  constexpr int U = kReduceUnroll;
   constexpr bool kPair = !std::is_same<S, double>::value;
+  using V = typename std::conditional<kPair, float, double>::type;
   double s[4] = {0, 0, 0, 0};
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   const int64_t t0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -190,29 +193,50 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a) {
       he[k] = 0.f;
     });
     int m = 0;
-    for (int64_t t = t0; t < a.ncells; t += stride) {
-      if (a.kind[t] != K_ACTIVE) continue;
-      const S* f = reinterpret_cast<const S*>(a.f) + (t / kCells) * Q * kCells + t % kCells;
-      if constexpr (!kPair) {
-        static_for<n>([&](auto k) { D[k] += f[(i0 + int(k)) * kCells]; });
-      } else {
+    for (int64_t t = t0; t < a.ncells; t += U * stride) {
+      // U cells t, t + stride, ...: kinds first, then every value at once
+      // (inactive cells contribute zeros)
+      bool on[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t tt = t + u * stride;
+        on[u] = tt < a.ncells && a.kind[tt] == K_ACTIVE;
+      }
+      V v[U][n];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t tt = t + u * stride;
+        const S* f = reinterpret_cast<const S*>(a.f) + (tt / kCells) * Q * kCells + tt % kCells;
         static_for<n>([&](auto k) {
-          // the stored value as the collision sees it (for FP16 the product
-          // h w rounded to float: __fmul_rn keeps the compiler from fusing
-          // it into the addition below, which would sum unrounded products)
-          float g;
+          constexpr int i = i0 + int(k);
           if constexpr (std::is_same<S, __half>::value)
-            g = __fmul_rn(__half2float(f[(i0 + int(k)) * kCells]), float(Lattice<Q>::w(i0 + int(k))));
+            // the stored value as the collision sees it: the product h w
+            // rounded to float (__fmul_rn keeps it from being fused into
+            // the addition below, which would sum unrounded products)
+            v[u][k] = on[u] ? __fmul_rn(__half2float(f[i * kCells]), float(Lattice<Q>::w(i))) : 0.f;
           else
-            g = Store<S>::template get<Q, i0 + int(k)>(f + (i0 + int(k)) * kCells);
-          // TwoSum: x = hs + g exactly equals x + r
-          const float x = hs[k] + g;
-          const float b = x - hs[k];
-          const float r = (hs[k] - (x - b)) + (g - b);
-          hs[k] = x;
-          he[k] += r;
+            v[u][k] = on[u] ? V(f[i * kCells]) : V(0);
         });
-        if (++m == kFlush) {
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        static_for<n>([&](auto k) {
+          if constexpr (!kPair) {
+            D[k] += v[u][k];
+          } else {
+            // TwoSum: x = hs + g exactly equals x + r
+            const float g = v[u][k];
+            const float x = hs[k] + g;
+            const float b = x - hs[k];
+            const float r = (hs[k] - (x - b)) + (g - b);
+            hs[k] = x;
+            he[k] += r;
+          }
+        });
+      }
+      if constexpr (kPair) {
+        m += U;
+        if (m >= kFlush) {
           static_for<n>([&](auto k) {
             D[k] += double(hs[k]);
             D[k] += double(he[k]);
