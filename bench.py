@@ -330,9 +330,10 @@ def run_jet3(lbm, torch, storage, steps, warmup, stream):
 
 
 def run_adjoint(lbm, torch, stream, T=256, every=16, N=96):
-    """Adjoint of the forced FCLB update (96^3, FP32, T = 256, checkpoints
-    every 16): device time of the T forward steps vs the checkpointed forward
-    and the recompute + adjoint backward sweep."""
+    """Adjoint of the forced FCLB update (96^3, FP32, T = 256): device time
+    of the T forward steps vs the recording forward and the backward sweep,
+    for checkpoints every `every` steps (recompute + adjoint) and for the
+    library's own choice (every state kept when it fits: no recompute)."""
     import synth
     omega = 1.0 / (3 * 0.005 + 0.5)
     rho, u = synth.spectrum_field(N, seed=4096)
@@ -350,48 +351,223 @@ def run_adjoint(lbm, torch, stream, T=256, every=16, N=96):
     e1.record(stream)
     e1.synchronize()
     fwd_ms = e0.elapsed_time(e1)
-    lbm.lbm_set_state(ctx, 0, f0)
-    e0.record(stream)
-    lbm.lbm_adjoint_forward(ctx, T, every)
-    e1.record(stream)
-    e1.synchronize()
-    ckfwd_ms = e0.elapsed_time(e1)
     lam = np.zeros((27, N, N, N))
     c = N // 2
     lam[:, c - 8:c + 8, c - 8:c + 8, c - 8:c + 8] = 1e-3
-    lbm.lbm_set_profiling(ctx, True)
-    lbm.lbm_adjoint_backward(ctx, lam)
-    pms, _ = lbm.lbm_get_profile(ctx)
-    lbm.lbm_set_profiling(ctx, False)
-    lbm.lbm_destroy(ctx)
-    sweep_ms = float(pms[4])
-    return {"grid": "%d^3" % N, "T": T, "checkpoint_every": every,
-            "forward_ms": round(fwd_ms, 3), "checkpointed_forward_ms": round(ckfwd_ms, 3),
-            "backward_sweep_ms": round(sweep_ms, 3),
-            "backward_over_forward": round(sweep_ms / fwd_ms, 3),
+    modes = {}
+    for ev in (every, 0):
+        lbm.lbm_set_state(ctx, 0, f0)
+        lbm.lbm_adjoint_forward(ctx, T, ev)       # allocation outside the timed pass
+        lbm.lbm_set_state(ctx, 0, f0)
+        lbm.lbm_sync(ctx)
+        e0.record(stream)
+        lbm.lbm_adjoint_forward(ctx, T, ev)
+        e1.record(stream)
+        e1.synchronize()
+        ckfwd_ms = e0.elapsed_time(e1)
+        used = lbm.lbm_adjoint_generation(ctx)[1]
+        lbm.lbm_set_profiling(ctx, True)
+        lbm.lbm_adjoint_backward(ctx, lam)
+        pms, _ = lbm.lbm_get_profile(ctx)
+        lbm.lbm_set_profiling(ctx, False)
+        sweep_ms = float(pms[4])
+        modes["auto" if ev == 0 else "every_%d" % ev] = {
+            "checkpoint_every": used, "recording_forward_ms": round(ckfwd_ms, 3),
+            "backward_sweep_ms": round(sweep_ms, 3), "backward_over_forward": round(sweep_ms / fwd_ms, 3),
             "adjoint_total_over_forward": round((ckfwd_ms + sweep_ms) / fwd_ms, 3)}
+    lbm.lbm_destroy(ctx)
+    return {"grid": "%d^3" % N, "T": T, "forward_ms": round(fwd_ms, 3), "modes": modes,
+            "adjoint_total_over_forward": modes["auto"]["adjoint_total_over_forward"]}
 
 
-def cpu_baseline(seconds=12.0):
-    """The FP64 oracle as it stands on the host cores: D3Q27 FCLB on a 16^3
-    periodic sample of the decaying-turbulence workload."""
+# D3Q27 velocities in the library's order (for the FP16 bound's constant)
+_E27 = np.array([[0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0, 1, -1, 1, 1, -1, -1, 1, -1],
+                 [0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1, 1, 1, -1, 1, -1, 1, -1, -1],
+                 [0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1, 1, 1, 1, -1, 1, -1, -1, -1]])
+_W27 = np.array([{0: 8 / 27, 1: 2 / 27, 2: 1 / 54, 3: 1 / 216}[int((_E27[:, i] ** 2).sum())] for i in range(27)])
+
+
+def fp16_bound_constant(f_cells):
+    """C = ||sqrt(sum_i |e_i|^2 g_i^2)||_2 / ||u||_2 over sampled cells
+    (f_cells [n][27], unshifted), g_i = f_i - w_i: one step of FP16 storage
+    rounds each g_i by at most 2^-11 |g_i|, so it moves the velocity of a
+    cell by at most 2^-11 sqrt(sum |e_i|^2 g_i^2) times a factor near one."""
+    g = f_cells - _W27[None, :]
+    rho = f_cells.sum(1)
+    u = (f_cells @ _E27.T) / rho[:, None]
+    inj = np.sqrt(((_E27 ** 2).sum(0)[None, :] * g * g).sum(1))
+    return float(np.sqrt((inj ** 2).sum()) / np.sqrt((u ** 2).sum()))
+
+
+def energy_spectrum(u, kmax):
+    """Shell-summed kinetic energy spectrum E(k), k = 1..kmax, of a periodic
+    field u [3][N][N][N] (E summed over |k| in [k - 1/2, k + 1/2))."""
+    N = u.shape[1]
+    uk = np.fft.rfftn(u, axes=(1, 2, 3)) / N ** 3
+    e = 0.5 * (np.abs(uk) ** 2).sum(0)
+    e[..., 1:(N + 1) // 2] *= 2.0          # the conjugate half of the rfft
+    kk = np.fft.fftfreq(N, d=1.0 / N)
+    kr = np.arange(uk.shape[-1])
+    kmag = np.sqrt(kk[:, None, None] ** 2 + kk[None, :, None] ** 2 + kr[None, None, :] ** 2)
+    shell = np.rint(kmag).astype(np.int64)
+    E = np.bincount(shell.ravel(), weights=e.ravel(), minlength=kmax + 1)
+    return E[1:kmax + 1]
+
+
+def run_config2_diagnostics(lbm, torch, field, stream, steps=2000, every=100):
+    """The 256^3 decaying-turbulence field (D3Q27 FCLB) run in FP64, FP32
+    and FP16 storage side by side for `steps` steps: kinetic energy and the
+    velocity relative L2 divergence of FP32/FP16 from FP64 every `every`
+    steps, energy spectra at t = 0, steps/2, steps, and the FP16 bound
+    sqrt(N) 2^-11 C beside its measured value (C from 65,536 sampled cells
+    of the initial state).  Not gated: the flow is chaotic, so rounding
+    differences grow exponentially and pass any rounding bound within about
+    a thousand steps (the bound is for non-chaotic flows, see
+    run_fp16_bound_laminar and the GPU tests)."""
+    cells = N_GRID ** 3
+    rho, u0 = field
+    ctxs = {}
+    for st in ("f64", "f32", "f16"):
+        ctxs[st] = lbm.lbm_create("d3q27", st, (N_GRID // 8,) * 3, True, [], OMEGA, 0.0, stream.cuda_stream)
+        lbm.lbm_init_equilibrium(ctxs[st], 0, rho, u0)
+    rng = np.random.default_rng(2000)
+    sample = rng.choice(cells, size=65536, replace=False).astype(np.int64)
+    C = fp16_bound_constant(lbm.lbm_get_cells(ctxs["f64"], 0, sample).reshape(-1, 27))
+    t0 = time.perf_counter()
+    energy = {st: [] for st in ctxs}
+    div = {"f32": [], "f16": []}
+    spectra = {}
+    kmax = 64
+    for t in range(0, steps + 1, every):
+        if t > 0:
+            for c in ctxs.values():
+                lbm.lbm_step(c, every)
+        us = {}
+        for st, c in ctxs.items():
+            _, us[st] = lbm.lbm_macroscopic(c, 0)
+            energy[st].append(float(0.5 * (us[st] ** 2).sum(0).mean()))
+        ref = us["f64"]
+        nref = float(np.sqrt((ref ** 2).sum()))
+        for st in div:
+            div[st].append(float(np.sqrt(((us[st] - ref) ** 2).sum())) / nref)
+        if t in (0, steps // 2, steps):
+            spectra[str(t)] = {st: [float("%.4g" % v) for v in energy_spectrum(us[st], kmax)] for st in ctxs}
+        del us, ref
+    for c in ctxs.values():
+        lbm.lbm_destroy(c)
+    ts = list(range(0, steps + 1, every))
+    bound = {str(n): math.sqrt(n) * 2.0 ** -11 * C for n in (100, 1000, 2000) if n <= steps}
+    measured = {str(n): div["f16"][ts.index(n)] for n in (100, 1000, 2000) if n in ts}
+    return {"grid": "256^3 periodic", "model": "d3q27", "steps": steps, "every": every,
+            "t": ts, "kinetic_energy": {k: [float("%.6g" % v) for v in e] for k, e in energy.items()},
+            "velocity_rel_l2_vs_f64": {k: [float("%.4g" % v) for v in d] for k, d in div.items()},
+            "spectra_k1_to_%d" % kmax: spectra,
+            "fp16_bound": {"form": "sqrt(N) * 2^-11 * C, C = ||sqrt(sum_i |e_i|^2 (f_i - w_i)^2)||_2 / ||u||_2 "
+                                   "at t = 0 (65,536 sampled cells)", "C": round(C, 5),
+                           "bound": {k: float("%.4g" % v) for k, v in bound.items()},
+                           "measured": {k: float("%.4g" % v) for k, v in measured.items()}},
+            "host_s": round(time.perf_counter() - t0, 1)}
+
+
+def run_fp16_bound_laminar(lbm, torch, stream, steps=1000):
+    """The FP16 bound on a non-chaotic flow of the same grid: a 256^3
+    Taylor-Green vortex (u0 = 0.04, D3Q27 FCLB, the decaying-turbulence
+    viscosity) in FP16 and FP32 storage against an FP64 run after `steps`
+    steps, beside the stated bound sqrt(N) 2^-11 C (C from 65,536 sampled
+    cells of the initial state)."""
+    import synth
+    cells = N_GRID ** 3
+    rho, u = synth.taylor_green_3d(N_GRID, 0.04)
+    out = {}
+    ctxs = {}
+    for st in ("f64", "f32", "f16"):
+        ctxs[st] = lbm.lbm_create("d3q27", st, (N_GRID // 8,) * 3, True, [], OMEGA, 0.0, stream.cuda_stream)
+        lbm.lbm_init_equilibrium(ctxs[st], 0, rho, u)
+    sample = np.random.default_rng(1000).choice(cells, size=65536, replace=False).astype(np.int64)
+    C = fp16_bound_constant(lbm.lbm_get_cells(ctxs["f64"], 0, sample).reshape(-1, 27))
+    for c in ctxs.values():
+        lbm.lbm_step(c, steps)
+    _, ref = lbm.lbm_macroscopic(ctxs["f64"], 0)
+    nref = float(np.sqrt((ref ** 2).sum()))
+    for st in ("f32", "f16"):
+        _, ug = lbm.lbm_macroscopic(ctxs[st], 0)
+        out[st] = float("%.4g" % (float(np.sqrt(((ug - ref) ** 2).sum())) / nref))
+        del ug
+    for c in ctxs.values():
+        lbm.lbm_destroy(c)
+    return {"case": "256^3 Taylor-Green vortex, u0 = 0.04, D3Q27 FCLB, nu = 1e-4, %d steps vs FP64 storage" % steps,
+            "C": round(C, 5), "bound": float("%.4g" % (math.sqrt(steps) * 2.0 ** -11 * C)),
+            "measured_f16": out["f16"], "measured_f32": out["f32"]}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def oracle_mlups(model, N, threads, steps=1):
+    """The FP64 oracle as it stands on an N^3 periodic sample of the
+    decaying-turbulence workload: MLUPS of `steps` timed steps (after one
+    untimed step) with `threads` torch threads."""
     import torch
     import synth
     from oracle.solver import NestedSolver
-    s = NestedSolver("d3q27", (2, 2, 2), periodic_x=True, omega=OMEGA)
-    rho, u = synth.spectrum_field(16, seed=1206)
-    s.init_equilibrium(0, torch.from_numpy(rho), torch.from_numpy(u))
-    s.step(1)
-    n, t0 = 0, time.perf_counter()
-    while True:
+    prev = torch.get_num_threads()
+    torch.set_num_threads(threads)
+    try:
+        s = NestedSolver(model, (N // 8,) * 3, periodic_x=True, omega=OMEGA, cs=0.1 if model == "d3q19" else 0.0)
+        rho, u = synth.spectrum_field(N, seed=1206)
+        s.init_equilibrium(0, torch.from_numpy(rho), torch.from_numpy(u))
         s.step(1)
-        n += 1
+        t0 = time.perf_counter()
+        s.step(steps)
         dt = time.perf_counter() - t0
-        if dt >= seconds and n >= 2:
-            break
-    return {"value": round(16 ** 3 * n / dt / 1e6, 6), "unit": "MLUPS", "cores": torch.get_num_threads(),
-            "kind": "oracle",
-            "sample": "D3Q27 FCLB FP64 oracle, 16^3 periodic sample of the k^4-spectrum field, %d steps in %.1f s" % (n, dt)}
+        used = torch.get_num_threads()
+    finally:
+        torch.set_num_threads(prev)
+    return N ** 3 * steps / dt / 1e6, dt, used
+
+
+def cpu_baseline(full=False, budget_s=60.0):
+    """The FP64 oracle on the host cores, per model, size and thread count:
+    64^3 with all cores and with one thread, 128^3 with all cores (and one
+    thread with full=True), one timed step each; a run stops adding cases
+    once the budget of timed seconds is spent.  The headline value is D3Q27
+    at 64^3 on all cores."""
+    import torch
+    cores = torch.get_num_threads()
+    cases = [("d3q27", 64, cores), ("d3q27", 64, 1), ("d3q19", 64, cores), ("d3q19", 64, 1),
+             ("d3q27", 128, cores), ("d3q19", 128, cores)]
+    if full:
+        cases += [("d3q27", 128, 1), ("d3q19", 128, 1)]
+    per, spent = [], 0.0
+    for model, N, th in cases:
+        if spent > budget_s:
+            per.append({"model": model, "grid": "%d^3" % N, "threads": th, "skipped": "time budget"})
+            continue
+        v, dt, used = oracle_mlups(model, N, th)
+        spent += dt
+        per.append({"model": model, "grid": "%d^3" % N, "threads": used, "mlups": round(v, 5),
+                    "step_s": round(dt, 2)})
+    head = per[0]
+    return {"value": head["mlups"], "unit": "MLUPS", "cores": head["threads"], "kind": "oracle",
+            "cpu_model": cpu_model(), "host_cores": os.cpu_count(),
+            "sample": "FP64 oracle (plain PyTorch CPU ops), one timed step per case on periodic samples of "
+                      "the k^4-spectrum workload; value = D3Q27 FCLB at 64^3 on all cores",
+            "per_case": per}
 
 
 def ours(args):
@@ -449,6 +625,24 @@ def ours(args):
                               "ms_per_coarse_step": {k: float(v) / K for k, v in
                                                      zip(["update", "c2f", "f2c", "bc", "other"], pms)},
                               "launches": [int(x) for x in pn]}), flush=True)
+        return
+    if args.kernel_only and args.variant.startswith("audit_"):
+        # the float64 mass/momentum audit (k_reduce) on an N^3 periodic grid
+        _, model, storage = args.variant.split("_")
+        N = args.grid
+        fld = synth.spectrum_field(N, seed=1206)
+        ctx = lbm.lbm_create(model, storage, (N // 8,) * 3, True, [], OMEGA, 0.0, stream.cuda_stream)
+        lbm.lbm_init_equilibrium(ctx, 0, *fld)
+        for _ in range(W):
+            lbm.lbm_mass_momentum(ctx)
+        t0 = time.perf_counter()
+        for _ in range(K):
+            m = lbm.lbm_mass_momentum(ctx)
+        dt = (time.perf_counter() - t0) / K
+        lbm.lbm_destroy(ctx)
+        if rank == 0:
+            print(json.dumps({"kernel_only": True, "variant": args.variant, "grid": N,
+                              "ms_per_audit_call": dt * 1e3, "sums": [float(v) for v in m]}), flush=True)
         return
     if args.kernel_only and args.variant == "adjoint":
         # the adjoint pipeline at 96^3 with a short horizon (profiling k_adjoint)
@@ -517,10 +711,9 @@ def ours(args):
     variants = {}
     errors = {}
     if not args.quick:
-        # FP64 reference run and storage error after a fixed number of steps
+        # FP64 storage throughput (its storage error is in config2_diagnostics)
         E = 100
         ref = run_uniform(lbm, torch, "d3q27", "f64", field, E, 0, stream)
-        _, ref_u = lbm.lbm_macroscopic(ref["ctx"], 0)
         variants["d3q27_f64"] = {"mlups": round(cells * E / (ref["ms"] * 1e-3) / 1e6, 1),
                                  "roofline_frac": roofline("d3q27", "f64", ref["kernel_ms"], cells)["frac"]}
         lbm.lbm_destroy(ref["ctx"])
@@ -531,11 +724,8 @@ def ours(args):
                 "mlups": round(cells * K / (r["ms"] * 1e-3) / 1e6, 1), "roofline_frac": rf["frac"],
                 "achieved_gbs": rf["achieved"], "tuning": list(r["tuning"])}
             lbm.lbm_destroy(r["ctx"])
-        for storage in ("f32", "f16"):
-            r = run_uniform(lbm, torch, "d3q27", storage, field, E, 0, stream)
-            errors["d3q27_%s_vs_f64_velocity_rel_l2_after_%d_steps" % (storage, E)] = \
-                velocity_error(lbm, r["ctx"], ref_u)
-            lbm.lbm_destroy(r["ctx"])
+        errors["fp16_bound_nonchaotic"] = run_fp16_bound_laminar(lbm, torch, stream)
+        errors["config2_diagnostics"] = run_config2_diagnostics(lbm, torch, field, stream)
         for model in ("d3q27", "d3q19"):
             variants["jet_2level_%s_f32" % model] = run_jet(lbm, torch, model, max(10, K // 4), 3, stream)
         # the same jet in a tank: no-slip side walls and bottom, free-slip top
@@ -567,7 +757,7 @@ def ours(args):
         "storage_error": errors,
     }
     if rank == 0 and world == 1:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(full=args.cpu_baseline_full)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -612,11 +802,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="headline only (no variants)")
+    ap.add_argument("--grid", type=int, default=256, help="for --kernel-only audit_*: N of the N^3 grid")
+    ap.add_argument("--cpu-baseline-full", action="store_true",
+                    help="also time the oracle single-threaded at 128^3 (minutes)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only the stream-collide steps of one variant (for ncu captures)")
     ap.add_argument("--variant", default="d3q27_f32",
                     help="for --kernel-only: model_storage (e.g. d3q19_f16), jet2s_/jet2t_/jet2p_/jet3s_/jet3p_"
-                         "model_storage, or adjoint")
+                         "model_storage, audit_model_storage, or adjoint")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
