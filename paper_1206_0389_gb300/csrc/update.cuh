@@ -32,6 +32,7 @@
 
 #include "collide.cuh"
 #include "kernels.cuh"
+#include "pair.cuh"
 
 namespace lbm {
 
@@ -234,30 +235,201 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
   }
 }
 
+// FP16 storage: each thread updates an x-adjacent pair of cells (c, c + 1),
+// c even, through the two-cell arithmetic of pair.cuh.  Packed FP32x2
+// instructions run the two collisions for about the instruction count of
+// one (the single-cell FP16 kernel was close to issue-bound), populations
+// with e_x = 0 come in as one aligned half2 load for both cells, and every
+// population leaves as one half2 store.  Pulls with e_x != 0 are two scalar
+// loads (their sources straddle the pair alignment).  Mixed pairs (one cell
+// masked out) store only the active cell.
+template <class M, int TPB, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) k_update_pair(const UpdateArgs a) {
+  using S = __half;
+  constexpr int Q = M::Q;
+  constexpr int QS = Q * kCells;
+  constexpr int NP = kCells / 2;  // pairs per block
+  const int pf_lane = threadIdx.x & 31;  // the population this lane prefetches
+  int pf_shift = 0;                      // its in-block pull shift e_x + 8 e_y + 64 e_z
+  static_for<Q>([&](auto i) {
+    if (pf_lane == int(i)) pf_shift = Lattice<Q>::ex(i) + 8 * Lattice<Q>::ey(i) + 64 * Lattice<Q>::ez(i);
+  });
+  for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+    const WorkItem w = a.items[it];
+    const LevelPtrs& L = a.lv[w.level];
+    const int BX = L.BX, BXY = L.BX * L.BY;
+    if (threadIdx.x == 0 && a.pf_ahead > 0 && it + a.pf_ahead < a.nitems) {
+      // the block a CTA about one wave later takes: its whole [Q][512] run
+      // (contiguous, 16-byte aligned) into L2 by one bulk prefetch of the
+      // TMA unit, so that CTA's loads find L2 instead of DRAM
+      const WorkItem wn = a.items[it + a.pf_ahead];
+      const char* pb = reinterpret_cast<const char*>(a.lv[wn.level].src) + int64_t(wn.block) * QS * int64_t(sizeof(S));
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pb), "r"(int(QS * sizeof(S))) : "memory");
+    }
+    // block deltas as in k_update (x / y offsets 32-bit, z widened per pair)
+    const int dxm = (w.edges & 1) ? (L.BX - 1) : -1;
+    const int dxp = (w.edges & 2) ? -(L.BX - 1) : 1;
+    const int dym = (w.edges & 4) ? BX * (L.BY - 1) : -BX;
+    const int dyp = (w.edges & 8) ? -BX * (L.BY - 1) : BX;
+    const int dzm = (w.edges & 16) ? BXY * (L.BZ - 1) : -BXY;
+    const int dzp = (w.edges & 32) ? -BXY * (L.BZ - 1) : BXY;
+    const V2 tau0 = V2(float(L.tau0), float(L.tau0));
+    const S* __restrict__ src = reinterpret_cast<const S*>(L.src) + int64_t(w.block) * QS;
+    S* __restrict__ dst = reinterpret_cast<S*>(L.dst) + int64_t(w.block) * QS;
+    auto active = [&](int c) {
+      if (w.mask < 0) return true;
+      const uint32_t m = __ldg(a.masks + w.mask * 16 + (c >> 5));
+      return bool((m >> (c & 31)) & 1u);
+    };
+#pragma unroll 1
+    for (int p = threadIdx.x; p < NP; p += TPB) {
+      const int c0 = 2 * p;
+      {
+        // the warp's next 64 cells: lane q asks L2 for the run of
+        // population q they pull (128 bytes, up to two lines)
+        const int cn = 2 * ((p & ~31) + TPB);
+        if (pf_lane < Q && cn < kCells) {
+          int sc = cn - pf_shift;
+          sc = sc < 0 ? 0 : sc > kCells - 1 ? kCells - 1 : sc;
+          const int se = sc + 63 > kCells - 1 ? kCells - 1 : sc + 63;
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(src + pf_lane * kCells + sc));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(src + pf_lane * kCells + se));
+        }
+      }
+      const bool a0 = active(c0), a1 = active(c0 + 1);
+      if (!a0 && !a1) continue;
+      const int x0 = c0 & 7, y = (c0 >> 3) & 7, z = c0 >> 6;
+      // cell c0 pulls e_x = +1 across the -x face when x0 == 0; cell c0 + 1
+      // pulls e_x = -1 across the +x face when x0 == 6 (from that cell itself
+      // on the zero-gradient outflow face)
+      const int Xm0 = (x0 == 0) ? dxm * QS + 8 : 0;
+      const int Xp1 = (x0 == 6) ? ((w.edges & 64) ? -1 : dxp * QS - 8) : 0;
+      const int Ym = (y == 0) ? dym * QS + 64 : 0;
+      const int Yp = (y == 7) ? dyp * QS - 64 : 0;
+      const S* p0 = src + c0;
+      const S* b1 = p0 + (z == 0 ? int64_t(dzm) * QS + 512 : int64_t(0));
+      const S* bm = p0 + (z == 7 ? int64_t(dzp) * QS - 512 : int64_t(0));
+      V2 g[Q];
+      static_for<Q>([&](auto i) {
+        constexpr int ex = Lattice<Q>::ex(i), ey = Lattice<Q>::ey(i), ez = Lattice<Q>::ez(i);
+        constexpr int k = int(i) * kCells - (ex + 8 * ey + 64 * ez);
+        int o = 0;
+        if constexpr (ey == 1) o += Ym;
+        if constexpr (ey == -1) o += Yp;
+        const S* b = ez == 1 ? b1 : ez == -1 ? bm : p0;
+        if constexpr (ex == 0) {
+          // both sources adjacent at an even element offset: one half2 load
+          const __half2 h = __ldg(reinterpret_cast<const __half2*>(b + o + k));
+          g[i] = V2(__low2float(h), __high2float(h));
+        } else if constexpr (ex == 1) {
+          g[i] = V2(__half2float(ldg_half_l2(b + o + k + Xm0)), __half2float(ldg_half_l2(b + o + k + 1)));
+        } else {
+          g[i] = V2(__half2float(ldg_half_l2(b + o + k)), __half2float(ldg_half_l2(b + o + k + 1 + Xp1)));
+        }
+      });
+      if constexpr (Q == 19) {
+        const V2 S_ = collide19<V2, true>(g, tau0, V2(float(a.cs2_18), float(a.cs2_18)));
+        if (L.aux_dst) {
+          float* ad = reinterpret_cast<float*>(L.aux_dst) + int64_t(w.block) * kCells + c0;
+          if (a0) ad[0] = S_.x;
+          if (a1) ad[1] = S_.y;
+        }
+      } else {
+        if (a.force != nullptr && w.level == 0) {
+          const int64_t n = int64_t(L.BX) * L.BY * L.BZ * kCells;
+          const int64_t j = int64_t(w.block) * kCells + c0;
+          const float* F = reinterpret_cast<const float*>(a.force);
+          collide27_closed<V2, true, true>(g, V2(1.0) / tau0, V2(F[j], F[j + 1]), V2(F[n + j], F[n + j + 1]),
+                                           V2(F[2 * n + j], F[2 * n + j + 1]));
+        } else {
+          collide27_closed<V2, false, true>(g, V2(1.0) / tau0, V2(0.0), V2(0.0), V2(0.0));
+        }
+      }
+      S* q = dst + c0;
+      if (a0 && a1) {
+        static_for<Q>([&](auto i) {
+          *reinterpret_cast<__half2*>(q + int(i) * kCells) = __floats2half2_rn(g[i].x, g[i].y);
+        });
+      } else if (a0) {
+        static_for<Q>([&](auto i) { q[int(i) * kCells] = __float2half_rn(g[i].x); });
+      } else {
+        static_for<Q>([&](auto i) { q[int(i) * kCells + 1] = __float2half_rn(g[i].y); });
+      }
+    }
+  }
+}
+
 // Launch shapes the autotuner chooses from: threads per CTA, and a minimum
 // number of resident CTAs per SM that caps the registers (higher occupancy
 // for the FP16 variants, whose half-size loads keep fewer bytes in flight).
+// FP16 storage without walls runs the cell-pair kernel; a listed shape maps
+// onto it with half the minimum CTAs per SM (two cells per thread hold about
+// twice the registers): (128,1) (256,1) (128,4) (256,2) (128,5).
+template <class M, int TPB, int MINB>
+cudaError_t launch_pair_shape(UpdateArgs a, int grid, bool persistent, cudaStream_t st) {
+  // prefetch distance: the CTAs resident at once (one CTA per block) or the
+  // grid (persistent CTAs take items grid apart)
+  static int occ = 0;  // CTAs per SM of this instance (a property of the kernel)
+  if (occ == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_pair<M, TPB, MINB>, TPB, 0);
+    if (e != cudaSuccess) return e;
+  }
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  a.pf_ahead = persistent ? grid : occ * sms;
+  k_update_pair<M, TPB, MINB><<<grid, TPB, 0, st>>>(a);
+  return cudaGetLastError();
+}
+template <class M>
+cudaError_t launch_pair(const UpdateArgs& a, int threads, int minb, int grid, bool persistent, cudaStream_t st) {
+  if (threads == 128 && minb == 7) return launch_pair_shape<M, 128, 5>(a, grid, persistent, st);
+  if (threads == 128 && minb == 1) return launch_pair_shape<M, 128, 1>(a, grid, persistent, st);
+  if (threads == 256 && minb == 1) return launch_pair_shape<M, 256, 1>(a, grid, persistent, st);
+  if (threads == 128 && minb == 8) return launch_pair_shape<M, 128, 4>(a, grid, persistent, st);
+  if (threads == 256 && minb == 4) return launch_pair_shape<M, 256, 2>(a, grid, persistent, st);
+  return cudaErrorInvalidValue;
+}
+template <class M>
+cudaError_t occ_pair(int threads, int minb, int* n) {
+  if (threads == 128 && minb == 7) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update_pair<M, 128, 5>, 128, 0);
+  if (threads == 128 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update_pair<M, 128, 1>, 128, 0);
+  if (threads == 256 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update_pair<M, 256, 1>, 256, 0);
+  if (threads == 128 && minb == 8) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update_pair<M, 128, 4>, 128, 0);
+  if (threads == 256 && minb == 4) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update_pair<M, 256, 2>, 256, 0);
+  return cudaErrorInvalidValue;
+}
+
 template <class M, class S, bool W>
 cudaError_t launch_ms(const UpdateArgs& a, int threads, int minb, int ctas, cudaStream_t st) {
   if (a.nitems == 0) return cudaSuccess;
   const int grid = ctas > 0 ? std::min(ctas, a.nitems) : a.nitems;
-  if (threads == 128 && minb == 7) k_update<M, S, 128, 7, W><<<grid, 128, 0, st>>>(a);
-  else if (threads == 128 && minb == 1) k_update<M, S, 128, 1, W><<<grid, 128, 0, st>>>(a);
-  else if (threads == 256 && minb == 1) k_update<M, S, 256, 1, W><<<grid, 256, 0, st>>>(a);
-  else if (threads == 128 && minb == 8) k_update<M, S, 128, 8, W><<<grid, 128, 0, st>>>(a);
-  else if (threads == 256 && minb == 4) k_update<M, S, 256, 4, W><<<grid, 256, 0, st>>>(a);
-  else return cudaErrorInvalidValue;
-  return cudaGetLastError();
+  if constexpr (std::is_same<S, __half>::value && !W) {
+    return launch_pair<M>(a, threads, minb, grid, ctas > 0, st);
+  } else {
+    if (threads == 128 && minb == 7) k_update<M, S, 128, 7, W><<<grid, 128, 0, st>>>(a);
+    else if (threads == 128 && minb == 1) k_update<M, S, 128, 1, W><<<grid, 128, 0, st>>>(a);
+    else if (threads == 256 && minb == 1) k_update<M, S, 256, 1, W><<<grid, 256, 0, st>>>(a);
+    else if (threads == 128 && minb == 8) k_update<M, S, 128, 8, W><<<grid, 128, 0, st>>>(a);
+    else if (threads == 256 && minb == 4) k_update<M, S, 256, 4, W><<<grid, 256, 0, st>>>(a);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+  }
 }
 
 template <class M, class S, bool W>
 cudaError_t occ_ms(int threads, int minb, int* n) {
-  if (threads == 128 && minb == 7) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 7, W>, 128, 0);
-  if (threads == 128 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 1, W>, 128, 0);
-  if (threads == 256 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 256, 1, W>, 256, 0);
-  if (threads == 128 && minb == 8) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 8, W>, 128, 0);
-  if (threads == 256 && minb == 4) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 256, 4, W>, 256, 0);
-  return cudaErrorInvalidValue;
+  if constexpr (std::is_same<S, __half>::value && !W) {
+    return occ_pair<M>(threads, minb, n);
+  } else {
+    if (threads == 128 && minb == 7) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 7, W>, 128, 0);
+    if (threads == 128 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 1, W>, 128, 0);
+    if (threads == 256 && minb == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 256, 1, W>, 256, 0);
+    if (threads == 128 && minb == 8) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 128, 8, W>, 128, 0);
+    if (threads == 256 && minb == 4) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, k_update<M, S, 256, 4, W>, 256, 0);
+    return cudaErrorInvalidValue;
+  }
 }
 
 // one translation unit per (model, storage) instantiates the periodic
