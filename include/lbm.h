@@ -151,7 +151,7 @@ int lbm_plan(const lbm_grid* g, int model, int storage, lbm_plan_info* out);
 int lbm_create(lbm_ctx** out, lbm_model model, lbm_storage storage, const lbm_grid* g,
                double omega, double cs, void* cuda_stream);
 
-/* Message of the last lbm_create failure on this thread ("" if none). */
+/* Message of the last lbm_create or lbm_shard_create failure on this thread ("" if none). */
 const char* lbm_create_error(void);
 
 /* Top-hat inflow on the face x = 0 (Section 3.2 names a constant inflow
@@ -354,6 +354,49 @@ int lbm_get_tuning(const lbm_ctx* ctx, int* threads, int* min_ctas_per_sm, int* 
 #define LBM_NOALLOC_MAX_BLOCKS 65536
 int lbm_mass_momentum_noalloc(int model, int storage, const void* f, int64_t nblocks, double* out,
                               void* cuda_stream);
+
+/* Block sharding (Sections 1 and 3.2: the paper partitions its blocks over
+ * processes, with a halo exchange of the populations that leave each
+ * partition).  The level-0 block columns along x are cut into nparts parts
+ * of balanced work (cells times substeps of every level above a column);
+ * each part is an ordinary context over its slab whose level-0 box keeps one
+ * halo block column beyond each cut.  Before each coarse step every cut
+ * exchanges, in both directions, the populations of the boundary cell layer
+ * that cross it (e_x = +1 one way, e_x = -1 the other: 9 of 27 or 5 of 19
+ * values per face cell): packed on the sender, copied device to device,
+ * unpacked into the receiver's halo.  Cuts lie only where no refined
+ * level-0 block is within one block of either side, so finer levels stay in
+ * one part and only level 0 has halos; a periodic x axis adds the cut
+ * between the last part and the first.  The inflow, the x walls, the outlet
+ * and the nozzle belong to the end parts (the nozzle, with a margin of 16
+ * coarse cells, must lie in part 0).  This build places every part on the
+ * calling thread's device.  The results equal the unsharded context's bit
+ * for bit when every context runs the same stream-collide variant
+ * (LBM_LAUNCH_SHAPE).  Dense arrays of lbm_shard_* calls are those of the
+ * whole grid, as for a context.  All return LBM_ERR_ARG for bad arguments,
+ * a grid the unsharded lbm_create rejects, or no admissible cuts. */
+typedef struct lbm_shard lbm_shard;
+/* The cuts (host only): cuts[0] = 0 < ... < cuts[nparts] = nbx, part p owning
+ * level-0 block columns [cuts[p], cuts[p + 1]). */
+int lbm_shard_plan(const lbm_grid* g, int nparts, int* cuts);
+int lbm_shard_create(lbm_shard** out, lbm_model model, lbm_storage storage, const lbm_grid* g, double omega,
+                     double cs, int nparts, void* cuda_stream);
+/* Context of one part (owned by the shard) and its level-0 block columns. */
+int lbm_shard_part(lbm_shard* s, int part, lbm_ctx** ctx, int* col0, int* col1);
+/* Bytes every coarse step moves across all cuts (both directions). */
+int lbm_shard_halo_bytes(const lbm_shard* s, int64_t* bytes_per_coarse_step);
+int lbm_shard_set_inflow(lbm_shard* s, double y0, double z0, double diameter, double u_in, double perturb,
+                         uint64_t seed);
+int lbm_shard_init_equilibrium(lbm_shard* s, int level, const double* rho, const double* u);
+/* Each coarse step: the halo exchange of every cut, then each part's step. */
+int lbm_shard_step(lbm_shard* s, int coarse_steps);
+int lbm_shard_sync(lbm_shard* s);
+int lbm_shard_get_state(lbm_shard* s, int level, double* f, size_t count);
+int lbm_shard_macroscopic(lbm_shard* s, int level, double* rho, double* u);
+/* Sum of the parts' float64 audits. */
+int lbm_shard_mass_momentum(lbm_shard* s, double out[4]);
+const char* lbm_shard_last_error(const lbm_shard* s);
+void lbm_shard_destroy(lbm_shard* s);  /* NULL-safe */
 
 /* Message describing the last failure on ctx ("" if none). */
 const char* lbm_last_error(const lbm_ctx* ctx);

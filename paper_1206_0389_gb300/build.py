@@ -15,7 +15,7 @@ SOURCES = ["update.cu", "update_d3q19_f64.cu", "update_d3q19_f32.cu", "update_d3
            "update_d3q27_f64.cu", "update_d3q27_f32.cu", "update_d3q27_f16.cu",
            "update_walls_d3q19_f64.cu", "update_walls_d3q19_f32.cu", "update_walls_d3q19_f16.cu",
            "update_walls_d3q27_f64.cu", "update_walls_d3q27_f32.cu", "update_walls_d3q27_f16.cu",
-           "interface.cu", "util.cu", "api.cu", "plan.cpp", "noalloc.cu", "adjoint.cu"]
+           "interface.cu", "util.cu", "api.cu", "plan.cpp", "noalloc.cu", "adjoint.cu", "shard.cu"]
 
 
 def nvcc():

@@ -588,6 +588,9 @@ bool all_finite(const double* p, size_t n) {
 
 }  // namespace
 
+int create_context(lbm_ctx** out, lbm_model model, lbm_storage storage, const lbm_grid* g, double omega,
+                   double cs, void* cuda_stream, const PlanOptions& opt);
+
 // ======================================================================= C ABI
 extern "C" {
 
@@ -621,6 +624,14 @@ const char* lbm_create_error(void) { return g_create_error.c_str(); }
 
 int lbm_create(lbm_ctx** out, lbm_model model, lbm_storage storage, const lbm_grid* g, double omega,
                double cs, void* cuda_stream) {
+  return create_context(out, model, storage, g, omega, cs, cuda_stream, PlanOptions());
+}
+
+}  // extern "C"
+
+// lbm_create with plan options (the parts of a sharded grid)
+int create_context(lbm_ctx** out, lbm_model model, lbm_storage storage, const lbm_grid* g, double omega,
+                   double cs, void* cuda_stream, const PlanOptions& opt) {
   g_create_error.clear();
   if (!out) {
     g_create_error = "out is NULL";
@@ -640,7 +651,7 @@ int lbm_create(lbm_ctx** out, lbm_model model, lbm_storage storage, const lbm_gr
     g_create_error = "host allocation failed";
     return LBM_ERR_OOM;
   }
-  std::string e = build_plan(*g, int(model), int(storage), omega, ctx->plan);
+  std::string e = build_plan(*g, int(model), int(storage), omega, ctx->plan, opt);
   if (!e.empty()) {
     g_create_error = e;
     delete ctx;
@@ -746,6 +757,8 @@ int lbm_create(lbm_ctx** out, lbm_model model, lbm_storage storage, const lbm_gr
   *out = ctx;
   return LBM_OK;
 }
+
+extern "C" {
 
 void lbm_destroy(lbm_ctx* ctx) {
   if (!ctx) return;
@@ -1426,3 +1439,11 @@ int lbm_get_tuning(const lbm_ctx* ctx, int* threads, int* min_ctas_per_sm, int* 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ access for the sharded grid (shard.cu)
+namespace lbm {
+void set_create_error(const std::string& m) { g_create_error = m; }
+const GridPlan& ctx_plan(const lbm_ctx* c) { return c->plan; }
+void* ctx_level0_buffer(lbm_ctx* c) { return c->dl[0].f[c->parity0]; }
+cudaStream_t ctx_stream(const lbm_ctx* c) { return c->stream; }
+}  // namespace lbm

@@ -35,7 +35,8 @@ enum CellKind : uint8_t {
   K_REFINED = 4,  // refined, deeper inside
   K_GHOST = 5,    // coarse-to-fine ghost cell
   K_BC = 6,       // inflow/outflow ghost cell
-  K_SOLID = 7     // inside the nozzle (not updated; its link populations are set)
+  K_SOLID = 7,    // inside the nozzle (not updated; its link populations are set)
+  K_HALO = 8      // halo column of a sharded part: a copy of the neighbouring part
 };
 
 struct LevelPtrs {

@@ -64,7 +64,8 @@ struct DomainLevel {
 
 }  // namespace
 
-std::string build_plan(const lbm_grid& g, int model, int storage, double omega, GridPlan& P) {
+std::string build_plan(const lbm_grid& g, int model, int storage, double omega, GridPlan& P,
+                       const PlanOptions& opt) {
   char msg[256];
   if (model != LBM_D3Q19_MRT_LES && model != LBM_D3Q27_FCLB) return "model must be 0 (D3Q19 MRT-LES) or 1 (D3Q27 FCLB)";
   if (storage != LBM_F64 && storage != LBM_F32 && storage != LBM_F16) return "storage must be 0 (F64), 1 (F32) or 2 (F16)";
@@ -100,6 +101,9 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
   P.slip = g.slip;
   P.outlet = g.outlet;
   const bool px = P.periodic_x;
+  if ((opt.halo_lo || opt.halo_hi) && px) return "internal: a sharded part has a non-periodic x axis";
+  if (opt.halo_lo && (g.walls & 16)) return "internal: a cut face cannot be the x = 0 wall";
+  if (opt.halo_hi && ((g.walls & 32) || g.outlet)) return "internal: a cut face cannot be the x = NX wall or outlet";
 
   // ---------------------------------------------------------------- levels
   std::vector<DomainLevel> D(L);
@@ -135,6 +139,16 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
                                                   ((g.walls & 16) && bx == 0) ||
                                                   ((g.walls & 32) && bx == d.nbx - 1))) {
                 snprintf(msg, sizeof msg, "refined block (%d,%d,%d) touches a wall face", bx, by, bz);
+                return msg;
+              }
+      }
+      if (l == 0 && (opt.halo_lo || opt.halo_hi)) {  // and away from the cuts of a sharded part
+        for (int bz = 0; bz < d.nbz; ++bz)
+          for (int by = 0; by < d.nby; ++by)
+            for (int bx = 0; bx < d.nbx; ++bx)
+              if (d.refined[d.at(bx, by, bz)] && ((opt.halo_lo && bx <= 1) || (opt.halo_hi && bx >= d.nbx - 2))) {
+                snprintf(msg, sizeof msg, "refined block (%d,%d,%d) within a block of a cut between parts", bx, by,
+                         bz);
                 return msg;
               }
       }
@@ -295,7 +309,7 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
           w.edges = uint8_t((lp.wrap[0] && X == 0 ? 1 : 0) | (lp.wrap[0] && X == lp.BX - 1 ? 2 : 0) |
                             (lp.wrap[1] && Y == 0 ? 4 : 0) | (lp.wrap[1] && Y == lp.BY - 1 ? 8 : 0) |
                             (lp.wrap[2] && Z == 0 ? 16 : 0) | (lp.wrap[2] && Z == lp.BZ - 1 ? 32 : 0) |
-                            (!px && !P.outlet && bx == d.nbx - 1 ? 64 : 0) |
+                            (!px && !P.outlet && !(l == 0 && opt.halo_hi) && bx == d.nbx - 1 ? 64 : 0) |
                             (l == 0 && (P.walls & 16) && bx == 0 ? 128 : 0));
           if (!d.refined[i]) {
             std::fill(k, k + 512, uint8_t(K_ACTIVE));
@@ -352,7 +366,22 @@ std::string build_plan(const lbm_grid& g, int model, int storage, double omega, 
         }
     // inflow ghost column x = -1 (the outflow needs none: the stream-collide
     // kernel reads its zero-gradient ghosts from x = NX - 1, edges bit 6)
+    // halo columns of a sharded part's cuts (level 0): copies of the
+    // neighbouring part's boundary layer, never updated
+    if (l == 0)
+      for (int side = 0; side < 2; ++side) {
+        if (!(side == 0 ? opt.halo_lo : opt.halo_hi)) continue;
+        for (int bz = 0; bz < d.nbz; ++bz)
+          for (int by = 0; by < d.nby; ++by) {
+            const int32_t hb = lp.box_id(side == 0 ? -1 : d.nbx, by, bz);
+            if (hb < 0) return "internal: halo block outside its box";
+            std::fill(&lp.kind[int64_t(hb) * 512], &lp.kind[int64_t(hb) * 512] + 512, uint8_t(K_HALO));
+          }
+      }
     if (!px) {
+      // (a cut face of a sharded part has no inflow: its halo is filled by
+      // the exchange)
+      if (!(l == 0 && opt.halo_lo))
       for (int bz = 0; bz < d.nbz; ++bz)
         for (int by = 0; by < d.nby; ++by) {
           if (!bcl[by + int64_t(d.nby) * bz]) continue;

@@ -56,8 +56,20 @@ struct GridPlan {
   int64_t device_bytes = 0;
 };
 
+// A part of a block-sharded grid (lbm_shard_*): its x faces marked here are
+// cuts between parts instead of domain faces.  The level-0 box then keeps one
+// halo block column beyond such a face, filled with the neighbouring part's
+// boundary layer before each coarse step; the face gets no inflow, outflow
+// or outlet, and no refined block may come within one block of it (finer
+// levels stay inside one part).
+struct PlanOptions {
+  bool halo_lo = false;  // the face x = 0 is a cut
+  bool halo_hi = false;  // the face x = NX is a cut
+};
+
 // Builds the plan; returns an empty string on success, else the reason.
-std::string build_plan(const lbm_grid& g, int model, int storage, double omega, GridPlan& out);
+std::string build_plan(const lbm_grid& g, int model, int storage, double omega, GridPlan& out,
+                       const PlanOptions& opt = PlanOptions());
 
 size_t storage_bytes(int storage);
 

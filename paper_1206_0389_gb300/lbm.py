@@ -27,7 +27,10 @@ EXPORTED = ["lbm_plan", "lbm_create", "lbm_create_error", "lbm_set_inflow", "lbm
             "lbm_mass_momentum_noalloc", "lbm_adjoint_forward", "lbm_adjoint_backward", "lbm_adjoint_generation",
             "lbm_get_strain", "lbm_set_strain", "lbm_raw_state_bytes", "lbm_get_raw_state",
             "lbm_set_raw_state", "lbm_stats_reset", "lbm_stats_accumulate", "lbm_stats_get",
-            "lbm_stats_radial", "lbm_jet_fit"]
+            "lbm_stats_radial", "lbm_jet_fit",
+            "lbm_shard_plan", "lbm_shard_create", "lbm_shard_part", "lbm_shard_halo_bytes", "lbm_shard_set_inflow",
+            "lbm_shard_init_equilibrium", "lbm_shard_step", "lbm_shard_sync", "lbm_shard_get_state",
+            "lbm_shard_macroscopic", "lbm_shard_mass_momentum", "lbm_shard_last_error", "lbm_shard_destroy"]
 NOALLOC_MAX_BLOCKS = 65536
 
 
@@ -102,6 +105,19 @@ def load():
         "lbm_adjoint_forward": (c_int, [c_void_p, c_int, c_int]),
         "lbm_adjoint_backward": (c_int, [c_void_p, D, D]),
         "lbm_adjoint_generation": (c_int, [c_void_p, P(c_uint64), P(c_int)]),
+        "lbm_shard_plan": (c_int, [P(lbm_grid), c_int, P(c_int)]),
+        "lbm_shard_create": (c_int, [P(c_void_p), c_int, c_int, P(lbm_grid), c_double, c_double, c_int, c_void_p]),
+        "lbm_shard_part": (c_int, [c_void_p, c_int, P(c_void_p), P(c_int), P(c_int)]),
+        "lbm_shard_halo_bytes": (c_int, [c_void_p, P(c_int64)]),
+        "lbm_shard_set_inflow": (c_int, [c_void_p, c_double, c_double, c_double, c_double, c_double, c_uint64]),
+        "lbm_shard_init_equilibrium": (c_int, [c_void_p, c_int, D, D]),
+        "lbm_shard_step": (c_int, [c_void_p, c_int]),
+        "lbm_shard_sync": (c_int, [c_void_p]),
+        "lbm_shard_get_state": (c_int, [c_void_p, c_int, D, c_size_t]),
+        "lbm_shard_macroscopic": (c_int, [c_void_p, c_int, D, D]),
+        "lbm_shard_mass_momentum": (c_int, [c_void_p, D]),
+        "lbm_shard_last_error": (c_char_p, [c_void_p]),
+        "lbm_shard_destroy": (None, [c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -383,3 +399,96 @@ def lbm_mass_momentum_noalloc(model, storage, f_ptr, nblocks, out_ptr, stream=No
                                           None if stream is None else c_void_p(int(stream)))
     if st != LBM_OK:
         raise LbmError(st, "lbm_mass_momentum_noalloc failed")
+
+
+# ------------------------------------------------------------------ block sharding
+class Shard(Context):
+    """An lbm_shard handle (the whole grid's sizes, as a Context) and its parts."""
+
+
+def _scheck(sh, st):
+    if st != LBM_OK:
+        msg = load().lbm_shard_last_error(sh.h if sh is not None else None)
+        raise LbmError(st, msg.decode() if msg else "")
+
+
+def lbm_shard_plan(nb, nparts, periodic_x=True, refine=(), walls=0, slip=0, outlet=0, nozzle=None):
+    """Level-0 block-column cuts of nparts parts: [0, c1, ..., nbx]."""
+    g, keep = make_grid(nb, periodic_x, refine, walls, slip, outlet, nozzle)
+    cuts = (c_int * (nparts + 1))()
+    st = load().lbm_shard_plan(ctypes.byref(g), int(nparts), cuts)
+    if st != LBM_OK:
+        raise LbmError(st, "no admissible cuts")
+    return list(cuts)
+
+
+def lbm_shard_create(model, storage, nb, periodic_x=True, refine=(), omega=1.0, cs=0.0, nparts=2, stream=None,
+                     walls=0, slip=0, outlet=0, nozzle=None):
+    lib = load()
+    g, keep = make_grid(nb, periodic_x, refine, walls, slip, outlet, nozzle)
+    h = c_void_p()
+    st = lib.lbm_shard_create(ctypes.byref(h), MODELS[model], STORAGES[storage], ctypes.byref(g), float(omega),
+                              float(cs), int(nparts), stream)
+    if st != LBM_OK:
+        raise LbmError(st, lib.lbm_create_error().decode())
+    sh = Shard(h, model, nb, g.levels)
+    sh.nparts = int(nparts)
+    return sh
+
+
+def lbm_shard_destroy(sh):
+    if sh is not None and sh.h:
+        load().lbm_shard_destroy(sh.h)
+        sh.h = None
+
+
+def lbm_shard_part(sh, part):
+    """(Context of the part, first level-0 column, one past its last)."""
+    h, c0, c1 = c_void_p(), c_int(), c_int()
+    _scheck(sh, load().lbm_shard_part(sh.h, int(part), ctypes.byref(h), ctypes.byref(c0), ctypes.byref(c1)))
+    nb = (c1.value - c0.value, sh.nb[1], sh.nb[2])
+    return Context(h, sh.model, nb, sh.levels), c0.value, c1.value
+
+
+def lbm_shard_halo_bytes(sh):
+    n = c_int64()
+    _scheck(sh, load().lbm_shard_halo_bytes(sh.h, ctypes.byref(n)))
+    return int(n.value)
+
+
+def lbm_shard_set_inflow(sh, y0, z0, diameter, u_in, perturb=0.01, seed=0):
+    _scheck(sh, load().lbm_shard_set_inflow(sh.h, y0, z0, diameter, u_in, perturb, int(seed)))
+
+
+def lbm_shard_init_equilibrium(sh, level, rho=None, u=None):
+    r, v = _f64(rho), _f64(u)
+    _scheck(sh, load().lbm_shard_init_equilibrium(sh.h, level, _dptr(r), _dptr(v)))
+
+
+def lbm_shard_step(sh, n=1):
+    _scheck(sh, load().lbm_shard_step(sh.h, int(n)))
+
+
+def lbm_shard_sync(sh):
+    _scheck(sh, load().lbm_shard_sync(sh.h))
+
+
+def lbm_shard_get_state(sh, level):
+    NX, NY, NZ = sh.dims(level)
+    f = np.empty((sh.Q, NZ, NY, NX))
+    _scheck(sh, load().lbm_shard_get_state(sh.h, level, _dptr(f), f.size))
+    return f
+
+
+def lbm_shard_macroscopic(sh, level):
+    NX, NY, NZ = sh.dims(level)
+    rho = np.empty((NZ, NY, NX))
+    u = np.empty((3, NZ, NY, NX))
+    _scheck(sh, load().lbm_shard_macroscopic(sh.h, level, _dptr(rho), _dptr(u)))
+    return rho, u
+
+
+def lbm_shard_mass_momentum(sh):
+    out = np.empty(4)
+    _scheck(sh, load().lbm_shard_mass_momentum(sh.h, _dptr(out)))
+    return out
