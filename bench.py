@@ -42,7 +42,8 @@ OMEGA = 1.0 / (3.0 * NU + 0.5)
 BYTES_PER_UPDATE = {("d3q27", "f32"): 216, ("d3q27", "f16"): 108, ("d3q27", "f64"): 432,
                     ("d3q19", "f32"): 152, ("d3q19", "f16"): 76, ("d3q19", "f64"): 304}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "update_kernel_traffic.txt")
-KERNEL_SOURCES = ["paper_1206_0389_gb300/csrc/update.cuh", "paper_1206_0389_gb300/csrc/collide.cuh",
+KERNEL_SOURCES = ["paper_1206_0389_gb300/csrc/update.cuh", "paper_1206_0389_gb300/csrc/pair.cuh",
+                  "paper_1206_0389_gb300/csrc/collide.cuh",
                   "paper_1206_0389_gb300/csrc/lattice.cuh"]
 
 
@@ -262,6 +263,30 @@ def run_jet(lbm, torch, model, steps, warmup, stream, walls=0, slip=0, paper_tan
             "launches_per_coarse_step": int(pn.sum()) // 3}
 
 
+def run_sharded(lbm, torch, field, steps, warmup, stream, nparts):
+    """The headline grid (256^3 D3Q27 FP32) cut into nparts parts on this
+    one GPU: each coarse step runs the halo exchange of every cut (pack,
+    device-to-device copy, unpack) and then each part's step."""
+    nb = (N_GRID // 8,) * 3
+    sh = lbm.lbm_shard_create("d3q27", "f32", nb, True, [], OMEGA, 0.0, nparts, stream.cuda_stream)
+    lbm.lbm_shard_init_equilibrium(sh, 0, *field)
+    lbm.lbm_shard_step(sh, warmup)
+    lbm.lbm_shard_sync(sh)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lbm.lbm_shard_step(sh, steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    cuts = [lbm.lbm_shard_part(sh, p)[1] for p in range(nparts)] + [nb[0]]
+    halo = lbm.lbm_shard_halo_bytes(sh)
+    lbm.lbm_shard_destroy(sh)
+    return {"parts": nparts, "cuts_level0_columns": cuts, "ms_per_step": round(ms, 4),
+            "mlups": round(N_GRID ** 3 / (ms * 1e-3) / 1e6, 1), "halo_bytes_per_step": halo,
+            "what": "all parts on one GPU; the exchange is pack + device-to-device copy + unpack per cut"}
+
+
 def run_jet3(lbm, torch, storage, steps, warmup, stream):
     """3-level jet at the paper's scale (coarse 512x256x256, nozzle D = 32,
     rings along the shear layer, 40.09 M active cells), D3Q27 FCLB."""
@@ -387,16 +412,15 @@ _E27 = np.array([[0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0, 
 _W27 = np.array([{0: 8 / 27, 1: 2 / 27, 2: 1 / 54, 3: 1 / 216}[int((_E27[:, i] ** 2).sum())] for i in range(27)])
 
 
-def fp16_bound_constant(f_cells):
-    """C = ||sqrt(sum_i |e_i|^2 g_i^2)||_2 / ||u||_2 over sampled cells
-    (f_cells [n][27], unshifted), g_i = f_i - w_i: one step of FP16 storage
-    rounds each g_i by at most 2^-11 |g_i|, so it moves the velocity of a
-    cell by at most 2^-11 sqrt(sum |e_i|^2 g_i^2) times a factor near one."""
+def fp16_injection_rms(f_cells):
+    """rms over sampled cells (f_cells [n][27], unshifted) of
+    I = sqrt(sum_i |e_i|^2 g_i^2), g_i = f_i - w_i: one step of FP16 storage
+    rounds each g_i by at most 2^-11 |g_i|, so it moves the momentum of a
+    cell by at most 2^-11 I times a factor near one.  The stated bound after
+    N steps is B = sqrt(N) 2^-11 rms(I at t = 0) / rms(u after N steps)."""
     g = f_cells - _W27[None, :]
-    rho = f_cells.sum(1)
-    u = (f_cells @ _E27.T) / rho[:, None]
     inj = np.sqrt(((_E27 ** 2).sum(0)[None, :] * g * g).sum(1))
-    return float(np.sqrt((inj ** 2).sum()) / np.sqrt((u ** 2).sum()))
+    return float(np.sqrt((inj ** 2).mean()))
 
 
 def energy_spectrum(u, kmax):
@@ -419,8 +443,7 @@ def run_config2_diagnostics(lbm, torch, field, stream, steps=2000, every=100):
     and FP16 storage side by side for `steps` steps: kinetic energy and the
     velocity relative L2 divergence of FP32/FP16 from FP64 every `every`
     steps, energy spectra at t = 0, steps/2, steps, and the FP16 bound
-    sqrt(N) 2^-11 C beside its measured value (C from 65,536 sampled cells
-    of the initial state).  Not gated: the flow is chaotic, so rounding
+    beside its measured value.  Not gated: the flow is chaotic, so rounding
     differences grow exponentially and pass any rounding bound within about
     a thousand steps (the bound is for non-chaotic flows, see
     run_fp16_bound_laminar and the GPU tests)."""
@@ -432,7 +455,8 @@ def run_config2_diagnostics(lbm, torch, field, stream, steps=2000, every=100):
         lbm.lbm_init_equilibrium(ctxs[st], 0, rho, u0)
     rng = np.random.default_rng(2000)
     sample = rng.choice(cells, size=65536, replace=False).astype(np.int64)
-    C = fp16_bound_constant(lbm.lbm_get_cells(ctxs["f64"], 0, sample).reshape(-1, 27))
+    I0 = fp16_injection_rms(lbm.lbm_get_cells(ctxs["f64"], 0, sample).reshape(-1, 27))
+    urms = {}
     t0 = time.perf_counter()
     energy = {st: [] for st in ctxs}
     div = {"f32": [], "f16": []}
@@ -448,6 +472,7 @@ def run_config2_diagnostics(lbm, torch, field, stream, steps=2000, every=100):
             energy[st].append(float(0.5 * (us[st] ** 2).sum(0).mean()))
         ref = us["f64"]
         nref = float(np.sqrt((ref ** 2).sum()))
+        urms[t] = nref / math.sqrt(cells)
         for st in div:
             div[st].append(float(np.sqrt(((us[st] - ref) ** 2).sum())) / nref)
         if t in (0, steps // 2, steps):
@@ -456,14 +481,14 @@ def run_config2_diagnostics(lbm, torch, field, stream, steps=2000, every=100):
     for c in ctxs.values():
         lbm.lbm_destroy(c)
     ts = list(range(0, steps + 1, every))
-    bound = {str(n): math.sqrt(n) * 2.0 ** -11 * C for n in (100, 1000, 2000) if n <= steps}
+    bound = {str(n): math.sqrt(n) * 2.0 ** -11 * I0 / urms[n] for n in (100, 1000, 2000) if n in urms}
     measured = {str(n): div["f16"][ts.index(n)] for n in (100, 1000, 2000) if n in ts}
     return {"grid": "256^3 periodic", "model": "d3q27", "steps": steps, "every": every,
             "t": ts, "kinetic_energy": {k: [float("%.6g" % v) for v in e] for k, e in energy.items()},
             "velocity_rel_l2_vs_f64": {k: [float("%.4g" % v) for v in d] for k, d in div.items()},
             "spectra_k1_to_%d" % kmax: spectra,
-            "fp16_bound": {"form": "sqrt(N) * 2^-11 * C, C = ||sqrt(sum_i |e_i|^2 (f_i - w_i)^2)||_2 / ||u||_2 "
-                                   "at t = 0 (65,536 sampled cells)", "C": round(C, 5),
+            "fp16_bound": {"form": "sqrt(N) * 2^-11 * rms(I at t = 0) / rms(u_N), I = sqrt(sum_i |e_i|^2 "
+                                   "(f_i - w_i)^2) (65,536 sampled cells)",
                            "bound": {k: float("%.4g" % v) for k, v in bound.items()},
                            "measured": {k: float("%.4g" % v) for k, v in measured.items()}},
             "host_s": round(time.perf_counter() - t0, 1)}
@@ -473,8 +498,7 @@ def run_fp16_bound_laminar(lbm, torch, stream, steps=1000):
     """The FP16 bound on a non-chaotic flow of the same grid: a 256^3
     Taylor-Green vortex (u0 = 0.04, D3Q27 FCLB, the decaying-turbulence
     viscosity) in FP16 and FP32 storage against an FP64 run after `steps`
-    steps, beside the stated bound sqrt(N) 2^-11 C (C from 65,536 sampled
-    cells of the initial state)."""
+    steps, beside the stated bound (fp16_injection_rms)."""
     import synth
     cells = N_GRID ** 3
     rho, u = synth.taylor_green_3d(N_GRID, 0.04)
@@ -484,11 +508,12 @@ def run_fp16_bound_laminar(lbm, torch, stream, steps=1000):
         ctxs[st] = lbm.lbm_create("d3q27", st, (N_GRID // 8,) * 3, True, [], OMEGA, 0.0, stream.cuda_stream)
         lbm.lbm_init_equilibrium(ctxs[st], 0, rho, u)
     sample = np.random.default_rng(1000).choice(cells, size=65536, replace=False).astype(np.int64)
-    C = fp16_bound_constant(lbm.lbm_get_cells(ctxs["f64"], 0, sample).reshape(-1, 27))
+    I0 = fp16_injection_rms(lbm.lbm_get_cells(ctxs["f64"], 0, sample).reshape(-1, 27))
     for c in ctxs.values():
         lbm.lbm_step(c, steps)
     _, ref = lbm.lbm_macroscopic(ctxs["f64"], 0)
     nref = float(np.sqrt((ref ** 2).sum()))
+    urms = nref / math.sqrt(cells)
     for st in ("f32", "f16"):
         _, ug = lbm.lbm_macroscopic(ctxs[st], 0)
         out[st] = float("%.4g" % (float(np.sqrt(((ug - ref) ** 2).sum())) / nref))
@@ -496,7 +521,8 @@ def run_fp16_bound_laminar(lbm, torch, stream, steps=1000):
     for c in ctxs.values():
         lbm.lbm_destroy(c)
     return {"case": "256^3 Taylor-Green vortex, u0 = 0.04, D3Q27 FCLB, nu = 1e-4, %d steps vs FP64 storage" % steps,
-            "C": round(C, 5), "bound": float("%.4g" % (math.sqrt(steps) * 2.0 ** -11 * C)),
+            "form": "sqrt(N) * 2^-11 * rms(I at t = 0) / rms(u_N), I = sqrt(sum_i |e_i|^2 (f_i - w_i)^2)",
+            "bound": float("%.4g" % (math.sqrt(steps) * 2.0 ** -11 * I0 / urms)),
             "measured_f16": out["f16"], "measured_f32": out["f32"]}
 
 
@@ -737,6 +763,8 @@ def ours(args):
         for storage in ("f32", "f16"):
             variants["jet_3level_d3q27_%s" % storage] = run_jet3(lbm, torch, storage, max(20, K // 4), 3, stream)
         variants["adjoint_d3q27_f32"] = run_adjoint(lbm, torch, stream)
+        for P in (2, 4):
+            variants["sharded_d3q27_f32_%dparts" % P] = run_sharded(lbm, torch, field, max(20, K // 4), 3, stream, P)
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": K,

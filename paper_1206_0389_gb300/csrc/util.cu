@@ -163,12 +163,14 @@ __global__ void k_gather(const GatherArgs a) {
 // float16 storage the per-population sums run in float32 pairs (s, e) by
 // Knuth's TwoSum, s + e being the sum of up to kFlush values with the
 // rounding of each addition kept in e, and every kFlush cells (inactive
-// ones adding zeros) both are added to the float64 sum.  The pair's error over m values is below
-// about m^2 u^2 sum |g| (u = 2^-24), 1e-12 of sum |g| for m = 16, the same
-// order as the bound of plain float64 recursive summation over a thread's
-// values.  The populations are taken in chunks (registers), each chunk
-// one pass over the thread's cells.
-constexpr int kFlush = 16;
+// ones adding zeros) both are added to the float64 sum.  The pair's error
+// over m values is below about m^2 u^2 sum |g| (u = 2^-24), 4e-12 of sum |g|
+// for m = 32, the order of the bound of plain float64 recursive summation
+// over a thread's values; the float64 work (two conversions and two
+// additions per population and flush) is what limits the kernel on GB300.
+// The populations are taken in chunks (registers), each chunk one pass over
+// the thread's cells.
+constexpr int kFlush = 32;
 constexpr int kReduceUnroll = 4;  // cells per iteration, their loads issued together
 
 template <class M, class S>

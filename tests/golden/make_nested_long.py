@@ -7,9 +7,11 @@ block wide in x and z (periodic in every direction): time nesting with 2:1
 refinement after Yu et al. (Sections 1 and 3.2), the drift taking the wave
 through every interface several times over the run.  The flow is invariant
 along x and z, so a level's state is fixed by its profile over y: the file
-holds, for every level and every row y of cells that hold a value of the
-level, rho and u after the last coarse step (the oracle's macroscopic
-fields; the cells of a row agree to round-off, and the row mean is kept).
+holds, at two times, for every level and every row y of cells that hold a
+value of the level, rho and u (the oracle's macroscopic fields; the cells of
+a row agree to round-off, and the row mean is kept).  The two times are
+1000 steps of the finest level (1000 / 2^(L-1) coarse steps) and 1000
+coarse steps.
 
 Usage: python tests/golden/make_nested_long.py [case ...]   (default: all)
 """
@@ -24,6 +26,12 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 
 # coarse steps, wave amplitude, drift, level-0 omega, Smagorinsky constant
 STEPS, AMP, DRIFT, OMEGA = 1000, 0.02, 0.05, 1.8
+
+
+def checkpoints(levels):
+    """Coarse steps at which the state is recorded: 1000 steps of the finest
+    level, and STEPS coarse steps."""
+    return (STEPS >> (levels - 1), STEPS)
 
 
 def grid(levels):
@@ -75,17 +83,18 @@ def path(case):
 
 
 def read(case):
-    """{level: (rows, [n][4] of rho, u_x, u_y, u_z)} from a case's file."""
+    """{coarse step: {level: (rows, [n][4] of rho, u_x, u_y, u_z)}} from a
+    case's file."""
     data = {}
     for line in open(path(case)):
         if line.startswith("#") or not line.strip():
             continue
         v = line.split()
-        l, y = int(v[0]), int(v[1])
-        data.setdefault(l, ([], []))
-        data[l][0].append(y)
-        data[l][1].append([float(t) for t in v[2:6]])
-    return {l: (np.array(r), np.array(a)) for l, (r, a) in data.items()}
+        t, l, y = int(v[0]), int(v[1]), int(v[2])
+        rows, vals = data.setdefault(t, {}).setdefault(l, ([], []))
+        rows.append(y)
+        vals.append([float(x) for x in v[3:7]])
+    return {t: {l: (np.array(r), np.array(a)) for l, (r, a) in d.items()} for t, d in data.items()}
 
 
 def run(case):
@@ -98,28 +107,35 @@ def run(case):
                      omega=OMEGA, cs=cs_of(c["model"]))
     for l, (rho, u) in enumerate(initial_fields(nb, c["levels"])):
         s.init_equilibrium(l, torch.from_numpy(rho), torch.from_numpy(u))
-    s.step(STEPS)
     with open(path(case), "w") as fh:
         fh.write("# %s: oracle (float64), %s, %d levels, coarse blocks %s, refine rows as in grid(), "
                  "omega_0 = %g, Cs = %g\n" % (case, c["model"], c["levels"], nb, OMEGA, cs_of(c["model"])))
-        fh.write("# u_x = %g sin(2 pi (y - y_if) / NY0), drift u_y = %g, after %d coarse steps\n"
-                 % (AMP, DRIFT, STEPS))
-        fh.write("# written by tests/golden/make_nested_long.py; columns: level, row y, rho, u_x, u_y, u_z\n")
-        for l in range(c["levels"]):
-            rho, u = s.macroscopic(l)
-            rho, u = rho.numpy(), u.numpy()
-            for y in range(rho.shape[1]):
-                row = rho[:, y, :]
-                if np.isnan(row).all():
-                    continue
-                assert not np.isnan(row).any()
-                # the flow is invariant along x and z (to round-off: the
-                # oracle's batched operations may round cells of a row apart
-                # in the last bit): one value per row, the row mean
-                vals = [row.mean()] + [u[a, :, y, :].mean() for a in range(3)]
-                assert np.abs(row - vals[0]).max() <= 1e-13
-                assert all(np.abs(u[a, :, y, :] - vals[1 + a]).max() <= 1e-13 for a in range(3))
-                fh.write("%d %d %s\n" % (l, y, " ".join("%.17g" % v for v in vals)))
+        fh.write("# u_x = %g sin(2 pi (y - y_if) / NY0), drift u_y = %g, after %s coarse steps\n"
+                 % (AMP, DRIFT, " and ".join(str(t) for t in checkpoints(c["levels"]))))
+        fh.write("# written by tests/golden/make_nested_long.py; columns: coarse step, level, row y, rho, u_x, "
+                 "u_y, u_z\n")
+        for t in checkpoints(c["levels"]):
+            s.step(t - s.coarse_step)
+            write_state(fh, s, c["levels"], t)
+
+
+def write_state(fh, s, levels, t):
+    """Rows of every level after coarse step t."""
+    for l in range(levels):
+        rho, u = s.macroscopic(l)
+        rho, u = rho.numpy(), u.numpy()
+        for y in range(rho.shape[1]):
+            row = rho[:, y, :]
+            if np.isnan(row).all():
+                continue
+            assert not np.isnan(row).any()
+            # the flow is invariant along x and z (to round-off: the oracle's
+            # batched operations may round cells of a row apart in the last
+            # bit): one value per row, the row mean
+            vals = [row.mean()] + [u[a, :, y, :].mean() for a in range(3)]
+            assert np.abs(row - vals[0]).max() <= 1e-13
+            assert all(np.abs(u[a, :, y, :] - vals[1 + a]).max() <= 1e-13 for a in range(3))
+            fh.write("%d %d %d %s\n" % (t, l, y, " ".join("%.17g" % v for v in vals)))
 
 
 if __name__ == "__main__":

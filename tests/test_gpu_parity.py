@@ -189,49 +189,50 @@ def test_velocity_l2_after_1000_steps_f32(model, N):
     close(ctx)
 
 
-def fp16_velocity_bound(f0, model, steps):
+def fp16_velocity_bound(f0, u_final, model, steps):
     """Stated bound on the velocity relative L2 error of FP16 storage after
-    `steps` steps: B = sqrt(N) 2^-11 C with
-        C = || sqrt(sum_i |e_i|^2 g_i^2) ||_2 / || u ||_2   (initial state),
+    `steps` steps: B = sqrt(N) 2^-11 ||I||_2 / ||u_N||_2 with
+        I = sqrt(sum_i |e_i|^2 g_i^2)   per cell, from the initial state,
     g_i the stored deviation (f_i - w_i for D3Q27, f_i for the incompressible
-    D3Q19 distribution).  One step stores every g_i with a relative rounding
-    of at most 2^-11 (half precision of g_i / w_i), which moves a cell's
-    momentum by at most sum_i |e_i| 2^-11 |g_i|; the roundings of different
-    values and steps are independent and unbiased (round to nearest), and
-    the stream-collide map does not amplify a perturbation of a stable
-    non-chaotic flow, so the error variances add: the L2 error after N steps
-    is about sqrt(N) 2^-11 C / sqrt(3) rms, and B allows sqrt(3) over it.
-    C is taken at t = 0, where the deviations of a decaying flow are largest."""
+    D3Q19 distribution) and u_N the velocity field after the N steps.  One
+    step stores every g_i with a relative rounding of at most 2^-11 (half
+    precision of g_i / w_i), which moves a cell's momentum by at most
+    sum_i |e_i| 2^-11 |g_i|; the roundings of different values and steps are
+    independent and unbiased (round to nearest), and the stream-collide map
+    does not amplify a perturbation of a stable non-chaotic flow, so the
+    error variances add: the absolute L2 error after N steps is about
+    sqrt(N) 2^-11 ||I|| / sqrt(3), and B allows sqrt(3) over it.  I is taken
+    at t = 0, where the deviations of a decaying flow are largest."""
     from oracle.lattice import velocities, weights
     Q = f0.shape[0]
-    e = velocities(Q).numpy().astype(np.float64)          # [3][Q]
+    e = velocities(Q).numpy().astype(np.float64).T        # [3][Q]
     w = weights(Q).numpy()
     f = f0.reshape(Q, -1)
     g = f - w[:, None] if model == "d3q27" else f
-    rho = f.sum(0) if model == "d3q27" else 1.0
-    u = (e @ f) / rho
     inj = np.sqrt(((e ** 2).sum(0)[:, None] * g * g).sum(0))
-    C = np.sqrt((inj ** 2).sum()) / np.sqrt((u ** 2).sum())
-    return math.sqrt(steps) * 2.0 ** -11 * C
+    return math.sqrt(steps) * 2.0 ** -11 * np.sqrt((inj ** 2).sum()) / np.sqrt((u_final ** 2).sum())
 
 
 @pytest.mark.parametrize("model,N", [("d3q19", 32), ("d3q27", 16)])
 def test_fp16_velocity_l2_after_1000_steps_within_stated_bound(model, N):
-    """Non-chaotic Taylor-Green flow, FP16 storage vs the FP64 oracle after
-    1000 steps: the measured velocity relative L2 error stays below the
-    stated bound sqrt(N) 2^-11 C (C from the initial state)."""
+    """Non-chaotic Taylor-Green flow (u0 = 0.03, nu = 0.002: the velocity
+    keeps about 80 % (32^3) or 40 % (16^3) of its amplitude), FP16 storage vs
+    the FP64 oracle after 1000 steps: the measured velocity relative L2 error
+    stays below the stated bound sqrt(N) 2^-11 ||I|| / ||u_N|| (I from the
+    initial state)."""
     lbm = gpu()
-    omega = 1.0 / (3 * 0.01 + 0.5)
+    omega = 1.0 / (3 * 0.002 + 0.5)
     nb = (N // 8,) * 3
     ctx, orc = make_pair(model, "f16", nb, omega=omega, cs=0.0)
     rho, u = synth.taylor_green_3d(N, 0.03)
     init_both(ctx, orc, [(rho, u)])
-    bound = fp16_velocity_bound(orc.state(0).numpy(), model, 1000)
+    f0 = orc.state(0).numpy()
     lbm.lbm_step(ctx, 1000)
     orc.step(1000)
     _, ug = lbm.lbm_macroscopic(ctx, 0)
     _, uo = orc.macroscopic(0)
     uo = uo.numpy()
+    bound = fp16_velocity_bound(f0, uo, model, 1000)
     l2 = np.sqrt(((ug - uo) ** 2).sum() / (uo ** 2).sum())
     print("FP16 velocity relative L2 after 1000 steps: %.3e, stated bound %.3e" % (l2, bound))
     assert l2 <= bound
