@@ -59,8 +59,8 @@ struct UpdateArgs {
                           // the faces x = 0 / x = NX, no-slip) and the free-slip ones
                           // among the y/z walls; read by the W = true kernels
   int pf_ahead;           // FP16 kernels: a CTA asks L2 for the block of work item
-                          // it + pf_ahead (about one wave ahead); 0 = off (set by the
-                          // launcher)
+                          // it + pf_ahead (about half a wave ahead); 0 = off (set by
+                          // the launcher)
 };
 
 // coarse-to-fine work comes in chunks of consecutive ghost cells (sorted by

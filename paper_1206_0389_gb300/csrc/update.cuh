@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_update_pair(const UpdateArgs a) {
     const LevelPtrs& L = a.lv[w.level];
     const int BX = L.BX, BXY = L.BX * L.BY;
     if (threadIdx.x == 0 && a.pf_ahead > 0 && it + a.pf_ahead < a.nitems) {
-      // the block a CTA about one wave later takes: its whole [Q][512] run
+      // the block a CTA about half a wave later takes: its whole [Q][512] run
       // (contiguous, 16-byte aligned) into L2 by one bulk prefetch of the
       // TMA unit, so that CTA's loads find L2 instead of DRAM
       const WorkItem wn = a.items[it + a.pf_ahead];
@@ -367,8 +367,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_update_pair(const UpdateArgs a) {
 // twice the registers): (128,1) (256,1) (128,4) (256,2) (128,5).
 template <class M, int TPB, int MINB>
 cudaError_t launch_pair_shape(UpdateArgs a, int grid, bool persistent, cudaStream_t st) {
-  // prefetch distance: the CTAs resident at once (one CTA per block) or the
-  // grid (persistent CTAs take items grid apart)
+  // prefetch distance: half the CTAs resident at once (one CTA per block:
+  // measured better than one or two full waves, whose prefetched blocks
+  // wait longer in L2) or the grid (persistent CTAs take items grid apart)
   static int occ = 0;  // CTAs per SM of this instance (a property of the kernel)
   if (occ == 0) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update_pair<M, TPB, MINB>, TPB, 0);
@@ -378,7 +379,7 @@ cudaError_t launch_pair_shape(UpdateArgs a, int grid, bool persistent, cudaStrea
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  a.pf_ahead = persistent ? grid : occ * sms;
+  a.pf_ahead = persistent ? grid : occ * sms / 2;
   k_update_pair<M, TPB, MINB><<<grid, TPB, 0, st>>>(a);
   return cudaGetLastError();
 }
