@@ -644,12 +644,22 @@ def ours(args):
                              outlet=outlet, nozzle=nozzle)
         lbm.lbm_set_inflow(ctx, centre[0], centre[1], D, 0.05, 0.01, 389)
         lbm.lbm_step(ctx, W)
+        # the coarse-step graphs (level-0 update beside the fine levels),
+        # then the same steps as sequential launches timed per kind
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lbm.lbm_step(ctx, K)
+        e1.record(stream)
+        e1.synchronize()
+        graph_ms = e0.elapsed_time(e1) / K
         lbm.lbm_set_profiling(ctx, True)
         lbm.lbm_step(ctx, K)
         pms, pn = lbm.lbm_get_profile(ctx)
         lbm.lbm_destroy(ctx)
         if rank == 0:
             print(json.dumps({"kernel_only": True, "variant": args.variant,
+                              "graph_ms_per_coarse_step": round(graph_ms, 4),
                               "ms_per_coarse_step": {k: float(v) / K for k, v in
                                                      zip(["update", "c2f", "f2c", "bc", "other"], pms)},
                               "launches": [int(x) for x in pn]}), flush=True)

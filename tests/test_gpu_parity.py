@@ -146,6 +146,35 @@ def test_nested_graph_and_direct_launches_agree(model, monkeypatch):
         assert np.array_equal(out[0][l], out[1][l])
 
 
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_three_level_graph_and_direct_launches_agree(model, storage, monkeypatch):
+    """Three levels with inflow on a grid large enough to fill the GPU (coarse
+    128 x 64 x 64): the coarse-step graph runs the first substep's level-0
+    update and the restriction into level 0 on branches beside the fine
+    levels' chain; it gives the same bits as the sequential launches of the
+    profiled path (one launch shape)."""
+    monkeypatch.setenv("LBM_LAUNCH_SHAPE", "128,8,0")
+    lbm = gpu()
+    nb = (16, 8, 8)
+    flags, (y0, z0) = synth.jet_three_level(*nb, r1=(0.0, 12.0), r2=(0.0, 8.0), x1=(0, 48), x2=(0, 24))
+    out = []
+    for prof in (False, True):
+        ctx = lbm.lbm_create(model, storage, nb, False, flags, 1.9, 0.18)
+        lbm.lbm_set_inflow(ctx, y0, z0, 8.0, 0.05, 0.01, 91)
+        for l in range(3):
+            NX, NY, NZ = ctx.dims(l)
+            rho, u = synth.taylor_green_3d(NY, 0.03, shape=(NX, NY, NZ))
+            lbm.lbm_init_equilibrium(ctx, l, rho, u)
+        lbm.lbm_set_profiling(ctx, prof)
+        lbm.lbm_step(ctx, 5)
+        lbm.lbm_sync(ctx)
+        out.append([lbm.lbm_get_raw_state(ctx, l) for l in range(3)])
+        close(ctx)
+    for l in range(3):
+        assert np.array_equal(out[0][l], out[1][l]), l
+
+
 def test_taylor_green_32_f64_200_steps():
     """32^3 Taylor-Green vortex, D3Q19 MRT + Smagorinsky (Cs = 0.1), FP64,
     u0 = 0.05, nu = 0.005, 200 steps: identical to the oracle to 1e-12, mass
