@@ -32,6 +32,8 @@ thread_local std::string g_create_error;
 
 struct Op {
   enum Kind { UPDATE, C2F, F2C, BC, LINK, INC } kind;
+  int k = 0;            // finest-level substep of the coarse step the op belongs to
+  bool level0 = false;  // an update of level-0 blocks alone (first substep of a nested grid)
   UpdateArgs ua{};
   C2FArgs ca{};
   F2CArgs fa{};
@@ -63,9 +65,10 @@ struct lbm_ctx {
   double omega = 1.0, cs = 0.0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  // second stream and events for the branch of the coarse-step graph that
-  // runs the inflow launch beside the coarse-to-fine launch
-  cudaStream_t side = nullptr;
+  // streams and events of the coarse-step graph's branches: the inflow
+  // launch beside the coarse-to-fine launch (side), and the fine-level chain
+  // (fine, high priority) beside the level-0 update (the capturing stream)
+  cudaStream_t side = nullptr, fine = nullptr;
   std::vector<cudaEvent_t> fork_join;
   int device = 0, sms = 1;
   std::vector<DevLevel> dl;
@@ -177,10 +180,19 @@ void free_all(lbm_ctx* c) {
   release_adjoint(c);
   for (cudaEvent_t e : c->fork_join) cudaEventDestroy(e);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->fine) cudaStreamDestroy(c->fine);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
 // --------------------------------------------------------------- schedule
+// Whether the coarse-step graph runs level 0's work beside the fine levels'
+// chain (nested grids with FP16 storage).  Measured on the paper-scale
+// 3-level jet: FP16 1.454 -> 1.427 ms per coarse step (its half-scale copy
+// 0.303 -> 0.280); FP32 2.100 -> 2.204 ms and the 2-level FP32 jets 1-2 %
+// slower, where the level-0 update is bandwidth-bound on its own and the
+// two branches only compete for DRAM and L2.
+bool split_level0(const lbm_ctx* c) { return c->L > 1 && c->storage == LBM_F16; }
+
 std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
   std::vector<Op> ops;
   const int L = c->L;
@@ -239,7 +251,10 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
         v.tau0_f = fp.tau0;
         a.n += v.n;
       }
-      if (a.n > 0) ops.push_back(op);
+      if (a.n > 0) {
+        op.k = k;
+        ops.push_back(op);
+      }
     }
     // inflow / outflow ghosts of the same levels (after the interface: an
     // inflow ghost may take its density from a coarse-to-fine ghost cell)
@@ -269,6 +284,7 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
         v.inv_scale = std::ldexp(1.0, -l);
         b.n += v.n;
       }
+      op.k = k;
       if (b.n > 0) ops.push_back(op);
     }
     // nozzle links of its level (after the level's previous update, before
@@ -292,6 +308,7 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
       a.u_in = c->u_in;
       a.perturb = c->perturb;
       a.seed = c->seed;
+      op.k = k;
       ops.push_back(op);
     }
     Op up;
@@ -316,6 +333,18 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
                                        : static_cast<const void*>(c->dl[0].force_f);
     u.walls = c->plan.walls;
     u.slip = c->plan.slip;
+    up.k = k;
+    if (lmin == 0 && split_level0(c)) {
+      // the first substep updates level 0 in a launch of its own: nothing
+      // reads its result before the midpoint of the coarse step, so the
+      // graph runs it beside the fine levels' first half
+      Op u0 = up;
+      u0.level0 = true;
+      u0.ua.nitems = int(c->list_len[0] - c->list_len[1]);
+      up.ua.items = c->items + c->list_off[1];
+      up.ua.nitems = int(c->list_len[1]);
+      ops.push_back(u0);
+    }
     ops.push_back(up);
     for (int l = lmin; l < L; ++l) par[l] ^= 1;
     // fine-to-coarse after the second substep of each fine level: one launch
@@ -341,11 +370,17 @@ std::vector<Op> build_schedule(lbm_ctx* c, int p0) {
         v.tau0_c = cp.tau0;
         v.tau0_f = fp.tau0;
         a.n += v.n;
+        op.level0 = l == 1;
       }
+      op.k = k;
+      // a restriction into level 0 alone: nothing later in the coarse step
+      // touches level 0, so the graph runs it beside the rest
+      op.level0 = op.level0 && a.nlv == 1 && split_level0(c);
       if (a.n > 0) ops.push_back(op);
     }
   }
   Op inc;
+  inc.k = K - 1;
   inc.kind = Op::INC;
   ops.push_back(inc);
   return ops;
@@ -400,6 +435,7 @@ int restrict_all(lbm_ctx* ctx) {
 }
 
 int build_graphs(lbm_ctx* ctx) {
+  const int K = 1 << (ctx->L - 1);
   for (int p = 0; p < 2; ++p) {
     if (ctx->graph[p]) {
       cudaGraphExecDestroy(ctx->graph[p]);
@@ -410,24 +446,78 @@ int build_graphs(lbm_ctx* ctx) {
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     size_t ev = 0;
+    auto next_event = [&](cudaEvent_t* out) {
+      if (ev >= ctx->fork_join.size()) return cudaErrorInvalidValue;
+      *out = ctx->fork_join[ev++];
+      return cudaSuccess;
+    };
+    // Nested FP16 grids: the chain of ops runs on the high-priority stream `fine`;
+    // the level-0 update of the first substep runs on the capturing stream
+    // beside it, after the level-0 inflow (and nozzle links) it reads, and
+    // joins the chain before the first op of the second half of the coarse
+    // step (the coarse-to-fine launch that reads level 0's new state, the
+    // restriction into level 0); that restriction in turn runs beside the
+    // rest of the chain (nothing after it touches level 0).  The level-0
+    // blocks fill the SMs the short interface launches leave idle.
+    const bool split = split_level0(ctx);
+    cudaStream_t st = ctx->stream;
+    cudaEvent_t u0_after = nullptr, u0_done = nullptr, r0_done = nullptr, evt = nullptr;
+    if (split) {
+      if ((e = next_event(&evt)) == cudaSuccess && (e = cudaEventRecord(evt, ctx->stream)) == cudaSuccess)
+        e = cudaStreamWaitEvent(ctx->fine, evt, 0);
+      st = ctx->fine;
+    }
     for (size_t k = 0; k < ops.size() && e == cudaSuccess; ++k) {
+      const Op& op = ops[k];
+      if (u0_done && op.k >= K / 2) {
+        if ((e = cudaStreamWaitEvent(st, u0_done, 0)) != cudaSuccess) break;
+        u0_done = nullptr;
+      }
       // the inflow launch after a coarse-to-fine launch touches other cells
       // (inflow ghosts fed by ghost cells are written by the latter), so the
       // graph runs the two side by side
-      if (ops[k].kind == Op::C2F && k + 1 < ops.size() && ops[k + 1].kind == Op::BC &&
-          ev + 1 < ctx->fork_join.size()) {
-        cudaEvent_t fork = ctx->fork_join[ev++], join = ctx->fork_join[ev++];
-        if ((e = cudaEventRecord(fork, ctx->stream)) != cudaSuccess ||
+      if (op.kind == Op::C2F && k + 1 < ops.size() && ops[k + 1].kind == Op::BC) {
+        cudaEvent_t fork = nullptr, join = nullptr;
+        if ((e = next_event(&fork)) != cudaSuccess || (e = next_event(&join)) != cudaSuccess ||
+            (e = cudaEventRecord(fork, st)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(ctx->side, fork, 0)) != cudaSuccess ||
             (e = run_op(ctx, ops[k + 1], ctx->side)) != cudaSuccess ||
-            (e = run_op(ctx, ops[k], ctx->stream)) != cudaSuccess ||
+            (e = run_op(ctx, op, st)) != cudaSuccess ||
             (e = cudaEventRecord(join, ctx->side)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(ctx->stream, join, 0)) != cudaSuccess)
+            (e = cudaStreamWaitEvent(st, join, 0)) != cudaSuccess)
           break;
+        if (ops[k + 1].k == 0) u0_after = join;  // the inflow is done
         ++k;
         continue;
       }
-      e = run_op(ctx, ops[k]);
+      if (split && op.level0 && op.kind == Op::UPDATE) {
+        if (u0_after && (e = cudaStreamWaitEvent(ctx->stream, u0_after, 0)) != cudaSuccess) break;
+        if ((e = run_op(ctx, op, ctx->stream)) != cudaSuccess || (e = next_event(&u0_done)) != cudaSuccess ||
+            (e = cudaEventRecord(u0_done, ctx->stream)) != cudaSuccess)
+          break;
+        continue;
+      }
+      if (split && op.level0 && op.kind == Op::F2C && !u0_done && !r0_done) {
+        // after the chain so far; joined at the end of the coarse step
+        cudaEvent_t here = nullptr;
+        if ((e = next_event(&here)) != cudaSuccess || (e = cudaEventRecord(here, st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->stream, here, 0)) != cudaSuccess ||
+            (e = run_op(ctx, op, ctx->stream)) != cudaSuccess || (e = next_event(&r0_done)) != cudaSuccess ||
+            (e = cudaEventRecord(r0_done, ctx->stream)) != cudaSuccess)
+          break;
+        continue;
+      }
+      if ((e = run_op(ctx, op, st)) != cudaSuccess) break;
+      if (split && op.k == 0 && (op.kind == Op::BC || (op.kind == Op::LINK && op.la.level == 0))) {
+        // the level-0 update waits for the chain up to here
+        if ((e = next_event(&u0_after)) != cudaSuccess || (e = cudaEventRecord(u0_after, st)) != cudaSuccess) break;
+      }
+    }
+    if (split && e == cudaSuccess) {
+      if (u0_done) e = cudaStreamWaitEvent(st, u0_done, 0);
+      if (r0_done && e == cudaSuccess) e = cudaStreamWaitEvent(st, r0_done, 0);
+      if (e == cudaSuccess && (e = next_event(&evt)) == cudaSuccess && (e = cudaEventRecord(evt, st)) == cudaSuccess)
+        e = cudaStreamWaitEvent(ctx->stream, evt, 0);
     }
     cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
     if (e != cudaSuccess) {
@@ -435,9 +525,10 @@ int build_graphs(lbm_ctx* ctx) {
       return cuda_fail(ctx, e, "capture");
     }
     if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&ctx->graph[p], g, 0);
+    // kernel nodes carry the priority of the stream they were captured from
+    e = cudaGraphInstantiateWithFlags(&ctx->graph[p], g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiateWithFlags");
   }
   ctx->graphs_valid = true;
   return LBM_OK;
@@ -682,9 +773,18 @@ int create_context(lbm_ctx** out, lbm_model model, lbm_storage storage, const lb
     if (ce != cudaSuccess) return bail(LBM_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(ce));
     ctx->own_stream = true;
   }
-  ce = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
-  if (ce != cudaSuccess) return bail(LBM_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(ce));
-  ctx->fork_join.assign(2 << (ctx->L - 1), nullptr);
+  {
+    // the fine-level chain of the coarse-step graph runs at the highest
+    // stream priority, the level-0 update beside it at the caller's
+    int least = 0, greatest = 0;
+    ce = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, greatest);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithPriority(&ctx->fine, cudaStreamNonBlocking, greatest);
+    if (ce != cudaSuccess) return bail(LBM_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(ce));
+  }
+  // events of one coarse-step capture: a fork and a join per coarse-to-fine
+  // launch, and at most six for the level-0 branches
+  ctx->fork_join.assign(2 * (1 << (ctx->L - 1)) + 8, nullptr);
   for (cudaEvent_t& e : ctx->fork_join) {
     ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
     if (ce != cudaSuccess) return bail(LBM_ERR_CUDA, std::string("event: ") + cudaGetErrorString(ce));
