@@ -9,8 +9,9 @@ over the second half of the run on the cells around the jet axis (the
 paper's centreline quantity, Section 3.3), u_x there after the last step,
 and rho and u of sampled cells of every level after the last step.
 
-Gates (relative to the largest |u| of the compared values): FP64 storage
-1e-9; FP32 storage 1e-4 (the velocity tolerance of the long-run tests)."""
+Gates (relative to the largest |u| of the compared values over all levels,
+about u_in): FP64 storage 1e-9; FP32 storage 1e-4 (the velocity tolerance of
+the long-run tests)."""
 import importlib.util
 import os
 
@@ -53,17 +54,20 @@ def run_gpu(storage, steps):
 def test_coarsened_paper_jet_against_stored_oracle_run(storage, tol):
     gold = C.read()
     got = run_gpu(storage, gold["steps"])
+    # one scale for every level: after the stored run the jet has not reached
+    # level 0's part of the axis, whose values there are round-off (~1e-15)
+    scale = max([np.abs(uo).max() for kind in ("mean", "final") for _, uo in gold[kind].values()] +
+                [np.abs(vals[:, 1:]).max() for _, vals in gold["cells"].values()])
+    assert scale > 0.01, scale
     worst = {}
     for kind in ("mean", "final"):
         for l, (xs, uo) in gold[kind].items():
             ug = got[kind][l][xs]
             assert np.isfinite(ug).all()
-            scale = max(np.abs(uo).max(), 1e-30)
             worst["%s_%d" % (kind, l)] = float(np.abs(ug - uo).max() / scale)
     for l, (idx, vals) in gold["cells"].items():
         rho, u = got["cells"][l]
         gu = np.stack([rho[idx], u[0][idx], u[1][idx], u[2][idx]], axis=1)
-        scale = max(np.abs(vals[:, 1:]).max(), 1e-30)
         worst["cells_u_%d" % l] = float(np.abs(gu[:, 1:] - vals[:, 1:]).max() / scale)
         worst["cells_rho_%d" % l] = float(np.abs(gu[:, 0] - vals[:, 0]).max())
     print(storage, "after %d coarse steps:" % gold["steps"], {k: "%.2e" % v for k, v in worst.items()})
