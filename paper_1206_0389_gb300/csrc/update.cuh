@@ -249,11 +249,6 @@ __global__ void __launch_bounds__(TPB, MINB) k_update_pair(const UpdateArgs a) {
   constexpr int Q = M::Q;
   constexpr int QS = Q * kCells;
   constexpr int NP = kCells / 2;  // pairs per block
-  const int pf_lane = threadIdx.x & 31;  // the population this lane prefetches
-  int pf_shift = 0;                      // its in-block pull shift e_x + 8 e_y + 64 e_z
-  static_for<Q>([&](auto i) {
-    if (pf_lane == int(i)) pf_shift = Lattice<Q>::ex(i) + 8 * Lattice<Q>::ey(i) + 64 * Lattice<Q>::ez(i);
-  });
   for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
     const WorkItem w = a.items[it];
     const LevelPtrs& L = a.lv[w.level];
@@ -284,18 +279,6 @@ __global__ void __launch_bounds__(TPB, MINB) k_update_pair(const UpdateArgs a) {
 #pragma unroll 1
     for (int p = threadIdx.x; p < NP; p += TPB) {
       const int c0 = 2 * p;
-      {
-        // the warp's next 64 cells: lane q asks L2 for the run of
-        // population q they pull (128 bytes, up to two lines)
-        const int cn = 2 * ((p & ~31) + TPB);
-        if (pf_lane < Q && cn < kCells) {
-          int sc = cn - pf_shift;
-          sc = sc < 0 ? 0 : sc > kCells - 1 ? kCells - 1 : sc;
-          const int se = sc + 63 > kCells - 1 ? kCells - 1 : sc + 63;
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(src + pf_lane * kCells + sc));
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(src + pf_lane * kCells + se));
-        }
-      }
       const bool a0 = active(c0), a1 = active(c0 + 1);
       if (!a0 && !a1) continue;
       const int x0 = c0 & 7, y = (c0 >> 3) & 7, z = c0 >> 6;
