@@ -330,8 +330,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_update_pair(const UpdateArgs a) {
       }
       S* q = dst + c0;
       if (a0 && a1) {
+        // streaming stores: the new state is not read again before the next
+        // step, so its lines go first when L2 needs room for prefetched blocks
         static_for<Q>([&](auto i) {
-          *reinterpret_cast<__half2*>(q + int(i) * kCells) = __floats2half2_rn(g[i].x, g[i].y);
+          __stcs(reinterpret_cast<__half2*>(q + int(i) * kCells), __floats2half2_rn(g[i].x, g[i].y));
         });
       } else if (a0) {
         static_for<Q>([&](auto i) { q[int(i) * kCells] = __float2half_rn(g[i].x); });

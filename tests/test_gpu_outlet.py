@@ -120,7 +120,8 @@ def test_outlet_per_step_reduced_precision(model, storage):
 
 
 @pytest.mark.parametrize("model", MODELS)
-def test_outlet_graph_and_direct_launches_agree(model, monkeypatch):
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_outlet_graph_and_direct_launches_agree(model, storage, monkeypatch):
     """The coarse-step graph (outlet and inflow launch beside the
     coarse-to-fine launch) and the sequential profiled launches give the same
     bits (one launch shape)."""
@@ -129,7 +130,7 @@ def test_outlet_graph_and_direct_launches_agree(model, monkeypatch):
     nb, ref = tank_jet()
     out = []
     for prof in (False, True):
-        ctx = lbm.lbm_create(model, "f32", nb, False, ref, 1.7, 0.18, walls=15, slip=8, outlet=1)
+        ctx = lbm.lbm_create(model, storage, nb, False, ref, 1.7, 0.18, walls=15, slip=8, outlet=1)
         lbm.lbm_set_outlet(ctx, 0.99)
         lbm.lbm_set_inflow(ctx, 12.0, 12.0, 12.0, 0.05, 0.01, 77)
         for l in range(2):
