@@ -196,28 +196,31 @@ __global__ void __launch_bounds__(256, 2) k_reduce(const ReduceArgs a) {
     });
     int m = 0;
     for (int64_t t = t0; t < a.ncells; t += U * stride) {
-      // U cells t, t + stride, ...: kinds first, then every value at once
-      // (inactive cells contribute zeros)
+      // U cells t, t + stride, ...: every value and kind loaded at once (the
+      // values unconditionally: every cell of the box has storage, so no
+      // load waits for a kind), then inactive cells select zeros
+      S raw[U][n];
       bool on[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int64_t tt = t + u * stride;
-        on[u] = tt < a.ncells && a.kind[tt] == K_ACTIVE;
+        const int64_t tc = tt < a.ncells ? tt : a.ncells - 1;
+        const S* f = reinterpret_cast<const S*>(a.f) + (tc / kCells) * Q * kCells + tc % kCells;
+        static_for<n>([&](auto k) { raw[u][k] = f[(i0 + int(k)) * kCells]; });
+        on[u] = tt < a.ncells && a.kind[tc] == K_ACTIVE;
       }
       V v[U][n];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int64_t tt = t + u * stride;
-        const S* f = reinterpret_cast<const S*>(a.f) + (tt / kCells) * Q * kCells + tt % kCells;
         static_for<n>([&](auto k) {
           constexpr int i = i0 + int(k);
           if constexpr (std::is_same<S, __half>::value)
             // the stored value as the collision sees it: the product h w
             // rounded to float (__fmul_rn keeps it from being fused into
             // the addition below, which would sum unrounded products)
-            v[u][k] = on[u] ? __fmul_rn(__half2float(f[i * kCells]), float(Lattice<Q>::w(i))) : 0.f;
+            v[u][k] = on[u] ? __fmul_rn(__half2float(raw[u][k]), float(Lattice<Q>::w(i))) : 0.f;
           else
-            v[u][k] = on[u] ? V(f[i * kCells]) : V(0);
+            v[u][k] = on[u] ? V(raw[u][k]) : V(0);
         });
       }
 #pragma unroll
