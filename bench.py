@@ -266,7 +266,8 @@ def run_jet(lbm, torch, model, steps, warmup, stream, walls=0, slip=0, paper_tan
 def run_sharded(lbm, torch, field, steps, warmup, stream, nparts):
     """The headline grid (256^3 D3Q27 FP32) cut into nparts parts on this
     one GPU: each coarse step runs the halo exchange of every cut (pack,
-    device-to-device copy, unpack) and then each part's step."""
+    device-to-device copy, unpack) and then each part's step, every part on
+    a stream of its own."""
     nb = (N_GRID // 8,) * 3
     sh = lbm.lbm_shard_create("d3q27", "f32", nb, True, [], OMEGA, 0.0, nparts, stream.cuda_stream)
     lbm.lbm_shard_init_equilibrium(sh, 0, *field)
@@ -284,7 +285,8 @@ def run_sharded(lbm, torch, field, steps, warmup, stream, nparts):
     lbm.lbm_shard_destroy(sh)
     return {"parts": nparts, "cuts_level0_columns": cuts, "ms_per_step": round(ms, 4),
             "mlups": round(N_GRID ** 3 / (ms * 1e-3) / 1e6, 1), "halo_bytes_per_step": halo,
-            "what": "all parts on one GPU; the exchange is pack + device-to-device copy + unpack per cut"}
+            "what": "all parts on one GPU, each on its own stream; the exchange is pack + device-to-device "
+                    "copy + unpack per cut"}
 
 
 def run_jet3(lbm, torch, storage, steps, warmup, stream):
@@ -664,6 +666,12 @@ def ours(args):
                                                      zip(["update", "c2f", "f2c", "bc", "other"], pms)},
                               "launches": [int(x) for x in pn]}), flush=True)
         return
+    if args.kernel_only and args.variant.startswith("sharded_"):
+        # the headline grid in P block-sharded parts (sharded_<P>)
+        r = run_sharded(lbm, torch, field, K, W, stream, int(args.variant.split("_")[1]))
+        if rank == 0:
+            print(json.dumps({"kernel_only": True, "variant": args.variant, **r}), flush=True)
+        return
     if args.kernel_only and args.variant.startswith("audit_"):
         # the float64 mass/momentum audit (k_reduce) on an N^3 periodic grid
         _, model, storage = args.variant.split("_")
@@ -849,7 +857,7 @@ def main():
                     help="only the stream-collide steps of one variant (for ncu captures)")
     ap.add_argument("--variant", default="d3q27_f32",
                     help="for --kernel-only: model_storage (e.g. d3q19_f16), jet2s_/jet2t_/jet2p_/jet3s_/jet3p_"
-                         "model_storage, audit_model_storage, or adjoint")
+                         "model_storage, audit_model_storage, adjoint, or sharded_<parts>")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

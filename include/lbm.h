@@ -388,7 +388,14 @@ int lbm_shard_halo_bytes(const lbm_shard* s, int64_t* bytes_per_coarse_step);
 int lbm_shard_set_inflow(lbm_shard* s, double y0, double z0, double diameter, double u_in, double perturb,
                          uint64_t seed);
 int lbm_shard_init_equilibrium(lbm_shard* s, int level, const double* rho, const double* u);
-/* Each coarse step: the halo exchange of every cut, then each part's step. */
+/* Each coarse step: the halo exchange of every cut, then each part's step.
+ * With more than one part every part steps on a stream of its own (created
+ * by the shard, so the parts' launches overlap as on separate devices); the
+ * exchange runs on cuda_stream after all work queued on the part streams,
+ * each part's step after the exchange, and cuda_stream waits for every part
+ * before the call returns, so work queued on cuda_stream afterwards (events,
+ * copies) sees the stepped state.  lbm_shard_sync waits for cuda_stream and
+ * every part stream. */
 int lbm_shard_step(lbm_shard* s, int coarse_steps);
 int lbm_shard_sync(lbm_shard* s);
 int lbm_shard_get_state(lbm_shard* s, int level, double* f, size_t count);

@@ -197,6 +197,15 @@ struct lbm_shard {
   std::vector<int> part_levels;  // levels of each part (finer levels only where its slab refines)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // each part steps on a stream of its own (the stand-in for a GPU of its
+  // own), joined to `stream` around the halo exchange by events
+  std::vector<cudaStream_t> pstream;
+  std::vector<cudaEvent_t> pevent;
+  cudaEvent_t exchanged = nullptr;
+  // one stream per cut and direction: the exchanges of different cuts and
+  // directions touch different layers and run side by side
+  std::vector<cudaStream_t> xstream;
+  std::vector<cudaEvent_t> xevent;
   Pops plus{}, minus{};
   // one cut: left part L, right part R (R = 0 for the periodic wrap); buffers
   // for L -> R (e_x = +1 values of L's last layer) and R -> L (e_x = -1 of
@@ -226,6 +235,11 @@ void shard_free(lbm_shard* s) {
     cudaFree(c.recv_rl);
   }
   for (lbm_ctx* p : s->parts) lbm_destroy(p);
+  for (cudaEvent_t e : s->pevent) cudaEventDestroy(e);
+  for (cudaStream_t t : s->pstream) cudaStreamDestroy(t);
+  for (cudaEvent_t e : s->xevent) cudaEventDestroy(e);
+  for (cudaStream_t t : s->xstream) cudaStreamDestroy(t);
+  if (s->exchanged) cudaEventDestroy(s->exchanged);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
 }
 
@@ -248,29 +262,41 @@ std::vector<uint8_t> slice_refine(const lbm_grid& g, int c0, int c1) {
 // c = nbx: high halo)
 int box_col(const lbm_ctx* part, int c) { return c - ctx_plan(part).lv[0].ox; }
 
+// The halo exchange of every cut, both directions, after all work queued on
+// `stream`: each direction (pack on the sender, device-to-device copy,
+// unpack into the receiver's halo) on a stream of its own; `exchanged` is
+// recorded on `stream` once all of them are done.
 int exchange(lbm_shard* s) {
-  for (auto& c : s->cut) {
+  cudaError_t e = cudaEventRecord(s->exchanged, s->stream);
+  for (size_t k = 0; k < s->cut.size() && e == cudaSuccess; ++k) {
+    const auto& c = s->cut[k];
     lbm_ctx *L = s->parts[c.L], *R = s->parts[c.R];
     const LevelPlan &pl = ctx_plan(L).lv[0], &pr = ctx_plan(R).lv[0];
     const int nl = pl.nbx;
-    cudaError_t e;
+    cudaStream_t lr = s->xstream[2 * k], rl = s->xstream[2 * k + 1];
+    if ((e = cudaStreamWaitEvent(lr, s->exchanged, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(rl, s->exchanged, 0)) != cudaSuccess)
+      break;
     // L's last layer x = 7 of column nl - 1, e_x = +1 -> R's low halo (column -1, layer 7)
     if ((e = halo_launch(true, s->storage, ctx_level0_buffer(L), s->Q, pl.BX, pl.BY, pl.BZ, box_col(L, nl - 1), 7,
-                         s->plus, c.send_lr, s->stream)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(c.recv_lr, c.send_lr, s->face_bytes_plus, cudaMemcpyDeviceToDevice, s->stream)) !=
-            cudaSuccess ||
+                         s->plus, c.send_lr, lr)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c.recv_lr, c.send_lr, s->face_bytes_plus, cudaMemcpyDeviceToDevice, lr)) != cudaSuccess ||
         (e = halo_launch(false, s->storage, ctx_level0_buffer(R), s->Q, pr.BX, pr.BY, pr.BZ, box_col(R, -1), 7,
-                         s->plus, c.recv_lr, s->stream)) != cudaSuccess)
-      return sfail(s, LBM_ERR_CUDA, std::string("halo exchange: ") + cudaGetErrorString(e));
+                         s->plus, c.recv_lr, lr)) != cudaSuccess)
+      break;
     // R's first layer x = 0 of column 0, e_x = -1 -> L's high halo (column nl, layer 0)
     if ((e = halo_launch(true, s->storage, ctx_level0_buffer(R), s->Q, pr.BX, pr.BY, pr.BZ, box_col(R, 0), 0,
-                         s->minus, c.send_rl, s->stream)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(c.recv_rl, c.send_rl, s->face_bytes_minus, cudaMemcpyDeviceToDevice, s->stream)) !=
-            cudaSuccess ||
+                         s->minus, c.send_rl, rl)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c.recv_rl, c.send_rl, s->face_bytes_minus, cudaMemcpyDeviceToDevice, rl)) != cudaSuccess ||
         (e = halo_launch(false, s->storage, ctx_level0_buffer(L), s->Q, pl.BX, pl.BY, pl.BZ, box_col(L, nl), 0,
-                         s->minus, c.recv_rl, s->stream)) != cudaSuccess)
-      return sfail(s, LBM_ERR_CUDA, std::string("halo exchange: ") + cudaGetErrorString(e));
+                         s->minus, c.recv_rl, rl)) != cudaSuccess)
+      break;
   }
+  for (size_t j = 0; j < s->xstream.size() && e == cudaSuccess; ++j)
+    if ((e = cudaEventRecord(s->xevent[j], s->xstream[j])) == cudaSuccess)
+      e = cudaStreamWaitEvent(s->stream, s->xevent[j], 0);
+  if (e == cudaSuccess) e = cudaEventRecord(s->exchanged, s->stream);
+  if (e != cudaSuccess) return sfail(s, LBM_ERR_CUDA, std::string("halo exchange: ") + cudaGetErrorString(e));
   return LBM_OK;
 }
 
@@ -343,6 +369,15 @@ int lbm_shard_create(lbm_shard** out, lbm_model model, lbm_storage storage, cons
     s->own_stream = true;
   }
   const bool px = g->periodic_x != 0;
+  if (nparts > 1) {
+    s->pstream.assign(nparts, nullptr);
+    s->pevent.assign(nparts, nullptr);
+    for (int p = 0; p < nparts; ++p)
+      if (cudaStreamCreateWithFlags(&s->pstream[p], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&s->pevent[p], cudaEventDisableTiming) != cudaSuccess)
+        return bail(LBM_ERR_CUDA);
+    if (cudaEventCreateWithFlags(&s->exchanged, cudaEventDisableTiming) != cudaSuccess) return bail(LBM_ERR_CUDA);
+  }
   s->part_refine.resize(nparts);
   for (int p = 0; p < nparts; ++p) {
     const int c0 = s->cuts[p], c1 = s->cuts[p + 1];
@@ -379,7 +414,7 @@ int lbm_shard_create(lbm_shard** out, lbm_model model, lbm_storage storage, cons
       gp.nozzle_x1 -= 8.0 * c0;
     }
     lbm_ctx* ctx = nullptr;
-    const int rc = create_context(&ctx, model, storage, &gp, omega, cs, s->stream, opt);
+    const int rc = create_context(&ctx, model, storage, &gp, omega, cs, nparts > 1 ? s->pstream[p] : s->stream, opt);
     if (rc != LBM_OK) {
       set_create_error("part " + std::to_string(p) + ": " + std::string(lbm_create_error()));
       return bail(rc);
@@ -396,6 +431,12 @@ int lbm_shard_create(lbm_shard** out, lbm_model model, lbm_storage storage, cons
     s->face_bytes_minus = size_t(s->minus.n) * layer * sb;
     for (int p = 0; p + 1 < nparts; ++p) s->cut.push_back(lbm_shard::Cut{p, p + 1});
     if (px) s->cut.push_back(lbm_shard::Cut{nparts - 1, 0});
+    s->xstream.assign(2 * s->cut.size(), nullptr);
+    s->xevent.assign(2 * s->cut.size(), nullptr);
+    for (size_t j = 0; j < s->xstream.size(); ++j)
+      if (cudaStreamCreateWithFlags(&s->xstream[j], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&s->xevent[j], cudaEventDisableTiming) != cudaSuccess)
+        return bail(LBM_ERR_CUDA);
     for (auto& c : s->cut)
       if (cudaMalloc(&c.send_lr, s->face_bytes_plus) != cudaSuccess ||
           cudaMalloc(&c.recv_lr, s->face_bytes_plus) != cudaSuccess ||
@@ -410,6 +451,8 @@ int lbm_shard_create(lbm_shard** out, lbm_model model, lbm_storage storage, cons
 void lbm_shard_destroy(lbm_shard* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
+  for (cudaStream_t t : s->pstream) cudaStreamSynchronize(t);
+  for (cudaStream_t t : s->xstream) cudaStreamSynchronize(t);
   shard_free(s);
   delete s;
 }
@@ -466,14 +509,34 @@ int lbm_shard_init_equilibrium(lbm_shard* s, int level, const double* rho, const
 int lbm_shard_step(lbm_shard* s, int coarse_steps) {
   if (!s) return LBM_ERR_ARG;
   if (coarse_steps < 0) return sfail(s, LBM_ERR_ARG, "coarse_steps must be >= 0");
+  if (s->P == 1) {
+    const int rc = lbm_step(s->parts[0], coarse_steps);
+    return rc ? sfail(s, rc, lbm_last_error(s->parts[0])) : LBM_OK;
+  }
+  // the exchange on `stream` after everything queued on the part streams
+  // (it reads each part's boundary layer of the current state), then every
+  // part's coarse step on its own stream after the exchange; at the end
+  // `stream` waits for all parts again
+  auto join_parts = [&]() -> int {
+    for (int p = 0; p < s->P; ++p) {
+      cudaError_t e = cudaEventRecord(s->pevent[p], s->pstream[p]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->pevent[p], 0);
+      if (e != cudaSuccess) return sfail(s, LBM_ERR_CUDA, std::string("join: ") + cudaGetErrorString(e));
+    }
+    return LBM_OK;
+  };
   for (int n = 0; n < coarse_steps; ++n) {
+    if (int rc = join_parts()) return rc;
     if (int rc = exchange(s)) return rc;
+    cudaError_t e = cudaSuccess;
+    for (int p = 0; p < s->P && e == cudaSuccess; ++p) e = cudaStreamWaitEvent(s->pstream[p], s->exchanged, 0);
+    if (e != cudaSuccess) return sfail(s, LBM_ERR_CUDA, std::string("fork: ") + cudaGetErrorString(e));
     for (lbm_ctx* p : s->parts) {
       const int rc = lbm_step(p, 1);
       if (rc) return sfail(s, rc, lbm_last_error(p));
     }
   }
-  return LBM_OK;
+  return join_parts();
 }
 
 int lbm_shard_get_state(lbm_shard* s, int level, double* f, size_t count) {
@@ -529,6 +592,7 @@ int lbm_shard_mass_momentum(lbm_shard* s, double out[4]) {
 int lbm_shard_sync(lbm_shard* s) {
   if (!s) return LBM_ERR_ARG;
   cudaError_t e = cudaStreamSynchronize(s->stream);
+  for (size_t p = 0; p < s->pstream.size() && e == cudaSuccess; ++p) e = cudaStreamSynchronize(s->pstream[p]);
   if (e != cudaSuccess) return sfail(s, LBM_ERR_CUDA, cudaGetErrorString(e));
   return LBM_OK;
 }

@@ -75,6 +75,15 @@ def test_uniform_periodic_sharded_bitwise(monkeypatch, model, nparts):
     assert halo == nparts * 2 * nq * 16 * 24 * 4
 
 
+def test_large_uniform_sharded_bitwise(monkeypatch):
+    """128^3 in 4 parts whose steps overlap on their own streams: every
+    exchange must wait for all parts' previous steps and every part's step
+    for the exchange (many CTAs, ten coarse steps)."""
+    nb = (16, 16, 16)
+    cuts, _ = run_both(monkeypatch, "d3q27", "f32", nb, 4, steps=10)
+    assert cuts == [0, 4, 8, 12, 16]
+
+
 @pytest.mark.parametrize("storage", ["f64", "f16"])
 def test_open_channel_with_inflow_sharded_bitwise(monkeypatch, storage):
     nb = (9, 2, 2)
