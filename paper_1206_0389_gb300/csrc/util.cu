@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256, 2) k_reduce(const ReduceArgs a) {
       hs[k] = 0.f;
       he[k] = 0.f;
     });
-    int m = 0;
+    [[maybe_unused]] int m = 0;  // cells since the last flush (float pairs only)
     for (int64_t t = t0; t < a.ncells; t += U * stride) {
       // U cells t, t + stride, ...: every value and kind loaded at once (the
       // values unconditionally: every cell of the box has storage, so no
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(256, 2) k_reduce(const ReduceArgs a) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         static_for<n>([&](auto k) {
-          constexpr int i = i0 + int(k);
+          [[maybe_unused]] constexpr int i = i0 + int(k);
           if constexpr (std::is_same<S, __half>::value)
             // the stored value as the collision sees it: the product h w
             // rounded to float (__fmul_rn keeps it from being fused into
