@@ -313,22 +313,42 @@ class NestedSolver:
             mirrored = torch.where(both, mir_yz, torch.where(only_y, mir_y, mir_z))
             pre[q] = torch.where(cross, torch.where(noslip, bounce, mirrored), pre[q])
 
-    def _update(self, l):
-        """Pull streaming and collision on the update mask of level l."""
+    def _update(self, l, inplace=False):
+        """Pull streaming and collision on the update mask of level l.
+
+        The pulled value of population i at cell x is f_i(x - e_i) with the
+        level array's periodic wrap (ghost columns included); with walls
+        (level 0) the whole rolled array is formed and the wall pulls replace
+        some of its entries, otherwise the same values are gathered at the
+        updated cells alone.  inplace: write the result into the level's own
+        arrays (the finest level, whose old state nothing reads)."""
         lv = self.levels[l]
         f = self.f[l]
-        pre = torch.empty_like(f)
-        for q in range(self.Q):
-            ex, ey, ez = (int(v) for v in self.m.e[q])
-            pre[q] = torch.roll(f[q], shifts=(ez, ey, ex), dims=(0, 1, 2))
-        if l == 0 and self.walls:
-            self._wall_pulls(f, pre)
         mask = lv.update
-        fin = pre[:, mask]
+        if l == 0 and self.walls:
+            pre = torch.empty_like(f)
+            for q in range(self.Q):
+                ex, ey, ez = (int(v) for v in self.m.e[q])
+                pre[q] = torch.roll(f[q], shifts=(ez, ey, ex), dims=(0, 1, 2))
+            self._wall_pulls(f, pre)
+            fin = pre[:, mask]
+        else:
+            if getattr(lv, "update_cells", None) is None:
+                lv.update_cells = torch.nonzero(mask, as_tuple=True)   # row-major, as mask indexing
+            zz, yy, xx = lv.update_cells
+            NZ, NY, NX = mask.shape
+            fin = torch.empty((self.Q, len(zz)), dtype=DTYPE)
+            for q in range(self.Q):
+                ex, ey, ez = (int(v) for v in self.m.e[q])
+                fin[q] = f[q, (zz - ez) % NZ, (yy - ey) % NY, (xx - ex) % NX]
         force = None
         if self.force is not None:
             force = self.force[:, self.real(l, mask).reshape(-1)]
         fout, sout = self.m.collide(fin, 1.0 / self._tau0(l), self.cs, force)
+        if inplace:
+            f[:, mask] = fout
+            self.S[l][mask] = sout
+            return f, self.S[l]
         new = f.clone()
         new[:, mask] = fout
         newS = self.S[l].clone()
@@ -409,13 +429,15 @@ class NestedSolver:
     def _advance(self, l, sub):
         self._apply_bc(l, sub)
         self._body_links(l, sub)
+        if l + 1 == self.L:
+            self._update(l, inplace=True)
+            return
         old, oldS = self.f[l].clone(), self.S[l].clone()
         new, newS = self._update(l)
-        if l + 1 < self.L:
-            for s in (0, 1):
-                self._c2f(l, s, old, new, oldS, newS)
-                self._advance(l + 1, 2 * sub + s)
-            self._f2c(l, new, newS)
+        for s in (0, 1):
+            self._c2f(l, s, old, new, oldS, newS)
+            self._advance(l + 1, 2 * sub + s)
+        self._f2c(l, new, newS)
         self.f[l], self.S[l] = new, newS
 
     # ------------------------------------------------------------ API
