@@ -27,7 +27,7 @@ PATH = os.path.join(HERE, "coarsened_jet.txt")
 
 NB = (16, 8, 8)
 D, U_IN, PERTURB, SEED, RE = 8.0, 0.05, 0.01, 5120, 1e4
-STEPS, SAMPLES = 36, 400
+STEPS, SAMPLES = 500, 400
 NU_C = U_IN * D / RE
 OMEGA = 1.0 / (3 * NU_C + 0.5)
 
