@@ -42,6 +42,13 @@ __device__ __forceinline__ __half ldg_half_l2(const __half* p) {
   asm("ld.global.nc.L2::256B.b16 %0, [%1];" : "=h"(v) : "l"(p));
   return __ushort_as_half(v);
 }
+// the same for float storage (the pulls of a warp's next rows then find
+// their sectors in L2: 0.5225 -> 0.5203 ms per 256^3 D3Q27 FP32 step)
+__device__ __forceinline__ float ldg_f32_l2(const float* p) {
+  float v;
+  asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
 
 template <class M, class S, int TPB, int MINB, bool W>
 __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
@@ -226,6 +233,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_update(const UpdateArgs a) {
         T g[Q];
         pull(c, [&](auto i, const S* p) {
           if constexpr (kScaled) g[i] = __half2float(ldg_half_l2(p));
+          else if constexpr (std::is_same<S, float>::value) g[i] = ldg_f32_l2(p);
           else g[i] = St::template get<Q, i>(p);
         });
         if constexpr (W) if (wf) wall_fix(c, g);
