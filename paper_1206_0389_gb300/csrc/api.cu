@@ -1175,7 +1175,7 @@ int lbm_jet_fit(int nbins, double dr, const double* mean_ux, const double* var_u
 
 int lbm_mass_momentum(lbm_ctx* ctx, double out[4]) {
   if (!ctx || !out) return fail(ctx, LBM_ERR_ARG, "NULL argument");
-  const int ctas = 2 * ctx->sms;  // one wave of the audit kernel (two CTAs per SM)
+  const int ctas = reduce_ctas_per_sm(ctx->storage) * ctx->sms;  // one wave of the audit kernel
   for (int l = 0; l < ctx->L; ++l) {
     ReduceArgs a{};
     a.f = ctx->dl[l].f[cur_parity(ctx, l)];

@@ -93,6 +93,10 @@ struct C2FItem {
 // of shared memory)
 __host__ __device__ constexpr int c2f_max_cells(int storage) { return storage == LBM_F64 ? 128 : 256; }
 constexpr int kC2FMaxItems = 128;  // = threads per CTA
+// resident 256-thread CTAs per SM of the float64 audit (one wave): three for
+// FP16 storage (0.373 -> 0.351 ms per 256^3 D3Q27 call), two otherwise
+// (three cost FP32 8 %)
+__host__ __device__ constexpr int reduce_ctas_per_sm(int storage) { return storage == LBM_F16 ? 3 : 2; }
 
 // fine-to-coarse: one hidden coarse cell and its 8 children as 4 x-pairs
 // (pair p = dy + 2 dz): the children (2X, ...) at fcell[p] and (2X+1, ...) at

@@ -174,7 +174,8 @@ constexpr int kFlush = 32;
 constexpr int kReduceUnroll = 4;  // cells per iteration, their loads issued together
 
 template <class M, class S>
-__global__ void __launch_bounds__(256, 2) k_reduce(const ReduceArgs a) {
+__global__ void __launch_bounds__(256, reduce_ctas_per_sm(std::is_same<S, __half>::value ? LBM_F16 : LBM_F32))
+    k_reduce(const ReduceArgs a) {
   constexpr int Q = M::Q;
   constexpr int P = Q == 19 ? 10 : 9;  // populations per pass
   constexpr int NP = (Q + P - 1) / P;
